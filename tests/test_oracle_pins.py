@@ -1,0 +1,221 @@
+"""Pins for the FP64 CPU oracle against facts fixed by the paper and by the mathematics, not by the oracle.
+
+* Brute force: the dense 2^n x 2^n operator of Sec. II.A (Kronecker product of the per-qubit gates,
+  Eq. tensor-product-gates) and of Sec. V.A (I x .. x Q_i x .. x I), built with numpy's ``kron`` and
+  multiplied onto the state, for n <= 7, every target and random control sets.
+* The paper's worked examples (fixtures under tests/golden/, each citing its passage).
+* Closed forms: QFT of a basis state, uniform state from H on every qubit, GHZ, circuit x inverse.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import circuits as C
+import oracle
+from conftest import golden_lines
+
+RNG = np.random.Generator(np.random.PCG64(20240601))
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# Dense Kronecker operator (the "direct approach" of Sec. IV applied to one gate): built independently of the
+# pair loop.  Little-endian reading: the leftmost Kronecker factor belongs to the highest qubit.
+# ----------------------------------------------------------------------------------------------------------------
+P0 = np.array([[1, 0], [0, 0]], dtype=np.complex128)
+P1 = np.array([[0, 0], [0, 1]], dtype=np.complex128)
+
+
+def kron_chain(factors_by_qubit):
+    """factors_by_qubit[q] is the 2x2 factor on qubit q; returns kron(f[n-1], ..., f[0])."""
+    out = np.array([[1.0 + 0j]])
+    for f in reversed(factors_by_qubit):
+        out = np.kron(out, f)
+    return out
+
+
+def dense_gate(n, u, target, controls=()):
+    """I - P_ctl (x) I_t + P_ctl (x) Q_t, with P_ctl the projector onto 'every control bit is 1'."""
+    ident = [C.I2] * n
+    full = kron_chain(ident)
+    if controls:
+        proj = [P1 if q in controls else C.I2 for q in range(n)]
+        proj_u = [P1 if q in controls else (u if q == target else C.I2) for q in range(n)]
+        return full - kron_chain(proj) + kron_chain(proj_u)
+    return kron_chain([u if q == target else C.I2 for q in range(n)])
+
+
+def dense_swap(n, a, b):
+    """SWAP = CNOT(a->b) CNOT(b->a) CNOT(a->b), each as a dense operator."""
+    c_ab = dense_gate(n, C.X, b, (a,))
+    c_ba = dense_gate(n, C.X, a, (b,))
+    return c_ab @ c_ba @ c_ab
+
+
+def rand_state(n):
+    v = RNG.standard_normal(2 ** n) + 1j * RNG.standard_normal(2 ** n)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7])
+def test_uncontrolled_gate_matches_kronecker_operator(n):
+    for t in range(n):
+        u = C.haar_u2(RNG)
+        psi = rand_state(n)
+        want = dense_gate(n, u, t) @ psi
+        got = oracle.apply_gate(psi.copy(), u, t)
+        assert np.max(np.abs(got - want)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7])
+def test_controlled_gate_matches_kronecker_operator(n):
+    for _ in range(12):
+        t = int(RNG.integers(n))
+        others = [q for q in range(n) if q != t]
+        m = int(RNG.integers(1, min(4, n - 1) + 1))
+        ctl = tuple(int(c) for c in RNG.choice(others, size=m, replace=False))
+        u = C.haar_u2(RNG)
+        psi = rand_state(n)
+        want = dense_gate(n, u, t, ctl) @ psi
+        got = oracle.apply_gate(psi.copy(), u, t, ctl)
+        assert np.max(np.abs(got - want)) < 1e-14, (t, ctl)
+
+
+@pytest.mark.parametrize("n", [2, 3, 6])
+def test_swap_matches_three_cnots(n):
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            psi = rand_state(n)
+            want = dense_swap(n, a, b) @ psi
+            got = oracle.apply_swap(psi.copy(), a, b)
+            assert np.array_equal(got, want)  # pure moves: bit-exact
+
+
+def test_circuit_is_product_of_gate_operators():
+    """A circuit is its gates applied in order (Sec. II.B): compare with the product of dense operators."""
+    n = 5
+    gates = C.random_layers(n, 3, RNG) + [C.gate_swap(0, 3), C.gate_u(C.haar_u2(RNG), 2, (0, 4))]
+    psi = rand_state(n)
+    want = psi.copy()
+    for g in gates:
+        op = dense_swap(n, g.target, g.target2) if g.kind == C.GATE_SWAP else dense_gate(n, g.u, g.target, g.controls)
+        want = op @ want
+    got = oracle.apply_circuit(psi.copy(), C.pack(gates))
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# The paper's worked examples
+# ----------------------------------------------------------------------------------------------------------------
+def test_pauli_x_and_hadamard_actions():
+    s = C.SQRT1_2
+    val = {"0": 0.0, "1": 1.0, "s": s, "-s": -s}
+    for gate, x, *amps in golden_lines("pauli_x_hadamard.txt"):
+        u = C.X if gate == "X" else C.H
+        got = oracle.apply_gate(oracle.basis_state(1, int(x)), u, 0)
+        want = np.array([val[amps[0]] + 1j * val[amps[1]], val[amps[2]] + 1j * val[amps[3]]])
+        assert np.array_equal(got, want)
+
+
+def test_cnot_truth_table():
+    for ket_in, ket_out in golden_lines("cnot_truth_table.txt"):
+        x_in, x_out = int(ket_in, 2), int(ket_out, 2)
+        got = oracle.apply_gate(oracle.basis_state(2, x_in), C.X, 0, (1,))
+        assert np.array_equal(got, oracle.basis_state(2, x_out))
+
+
+def test_pair_strides_n3():
+    """X on qubit i sends |k> to its partner: the pairs of Fig. 'statevector' (stride 2^i)."""
+    for row in golden_lines("pair_strides_n3.txt"):
+        q = int(row[0].rstrip(":"))
+        for pair in row[1:]:
+            a, b = (int(v) for v in pair.split("-"))
+            assert np.array_equal(oracle.apply_gate(oracle.basis_state(3, a), C.X, q), oracle.basis_state(3, b))
+            assert np.array_equal(oracle.apply_gate(oracle.basis_state(3, b), C.X, q), oracle.basis_state(3, a))
+
+
+def test_tensor_product_two_qubits():
+    """Preparing qubit 1 in psi0 and qubit 0 in psi1 gives Eq. tensor-product-2qubit-example."""
+    u0, u1 = C.haar_u2(RNG), C.haar_u2(RNG)
+    a0, b0 = u0[:, 0]
+    a1, b1 = u1[:, 0]
+    f = {"a0": a0, "b0": b0, "a1": a1, "b1": b1}
+    psi = oracle.basis_state(2, 0)
+    oracle.apply_gate(psi, u0, 1)
+    oracle.apply_gate(psi, u1, 0)
+    for idx, left, right in golden_lines("tensor_product_2q.txt"):
+        assert abs(psi[int(idx)] - f[left] * f[right]) < 1e-15
+
+
+def test_non_sequential_storage_example():
+    """Sec. VI.B: interchanging index bits 1 and 2 of an n = 3 vector stores alpha_0,1,4,5,2,3,6,7."""
+    order = [int(v) for v in golden_lines("nonsequential_order_n3.txt")[0]]
+    psi = np.arange(8, dtype=np.complex128) * (1 + 0.5j)
+    got = oracle.apply_swap(psi.copy(), 1, 2)
+    assert np.array_equal(got, psi[order])
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# Closed forms and invariants
+# ----------------------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 10])
+def test_qft_closed_form(n):
+    gates = C.pack(C.qft(n))
+    assert len(gates) == n + n * (n - 1) // 2 + n // 2
+    ys = np.arange(2 ** n)
+    for x in sorted({0, 1, 2 ** n - 1, int(RNG.integers(2 ** n))}):
+        got = oracle.simulate(n, gates, x)
+        want = np.exp(2j * np.pi * ((x * ys) % 2 ** n) / 2 ** n) / math.sqrt(2 ** n)
+        assert np.max(np.abs(got - want)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 4, 11])
+def test_hadamard_on_every_qubit_gives_uniform_state(n):
+    got = oracle.simulate(n, C.pack(C.hadamard_all(n)))
+    assert np.max(np.abs(got - 2.0 ** (-n / 2))) < 1e-15
+    assert np.all(got.imag == 0)
+
+
+@pytest.mark.parametrize("n", [2, 3, 9])
+def test_ghz_exact(n):
+    got = oracle.simulate(n, C.pack(C.ghz(n)))
+    want = np.zeros(2 ** n, dtype=np.complex128)
+    want[0] = want[-1] = C.SQRT1_2
+    assert np.array_equal(got, want)  # H|0> = (s, s) exactly, the CNOTs only move amplitudes
+
+
+def test_circuit_followed_by_inverse_is_identity():
+    n = 8
+    g = C.pack(C.random_layers(n, 10, RNG) + C.qft(n))
+    psi = oracle.simulate(n, np.concatenate([g, C.inverse(g)]))
+    assert abs(psi[0] - 1) < 1e-13
+    assert np.max(np.abs(psi[1:])) < 1e-13
+
+
+def test_norm_is_preserved():
+    n = 10
+    psi = oracle.simulate(n, C.random_workload(n, 5, seed=7).gates)
+    assert abs(oracle.norm2(psi) - 1.0) < 1e-13
+    assert abs(np.sum(oracle.probabilities(psi)) - 1.0) < 1e-13
+
+
+def test_thread_count_does_not_change_result():
+    n = 12
+    w = C.random_workload(n, 3, seed=11)
+    a = oracle.simulate(n, w.gates, threads=1)
+    b = oracle.simulate(n, w.gates, threads=4)
+    assert np.array_equal(a, b)
+
+
+def test_rejects_malformed_gates():
+    psi = oracle.basis_state(3)
+    with pytest.raises(ValueError):
+        oracle.apply_gate(psi, C.X, 3)
+    with pytest.raises(ValueError):
+        oracle.apply_gate(psi, C.X, 1, (1,))
+    with pytest.raises(ValueError):
+        oracle.apply_gate(psi, C.X, 1, (0, 0))
+    with pytest.raises(ValueError):
+        oracle.apply_swap(psi, 2, 2)
