@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector gate path on GB300.
+
+Workload (one "step"): start from |0...0> on n = 30 qubits, apply the seeded 20-layer random circuit (each
+layer: a Haar-random U(2) on every qubit, then CNOTs on a random perfect matching; 900 gates, seed 1002),
+then reduce the norm in double precision and read 1024 amplitudes back to the host.  The headline is
+complex128 (IEEE double storage, 16 GiB state); complex64 is measured on the same circuit for comparison.
+
+Reported: gates/s (value), effective HBM GB/s (2 * state bytes per gate, i.e. every gate counted as one
+unfused read+write sweep), the dominant kernel's roofline (CUDA events around its launches inside the
+timed region), the FP64 CPU oracle timed on the host's cores on a bounded sample, an end-to-end number
+through the C ABI with host buffers, SM clocks sampled during the timed region.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a device synchronize; CUDA events
+on the launching (legacy default) stream; the state (16 GiB) is larger than L2, so no flush is needed.
+With torchrun (N > 1) every rank runs its own replica (weak scaling, no collective on the data path); the
+reported time is the maximum over ranks and the value the total gates of all ranks divided by it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+RANK = int(os.environ.get("RANK", "0"))
+WORLD = int(os.environ.get("WORLD_SIZE", "1"))
+LOCAL_RANK = int(os.environ.get("LOCAL_RANK", "0"))
+if WORLD > 1:
+    # One GPU per process: the library's CUDA runtime sees only this rank's device.
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    devs = vis.split(",") if vis else [str(i) for i in range(64)]
+    os.environ["CUDA_VISIBLE_DEVICES"] = devs[LOCAL_RANK]
+
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import circuits as C  # noqa: E402
+
+N_QUBITS = 30
+DEPTH = 20
+SEED = 1002
+READ_COUNT = 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--depth", type=int, default=DEPTH)
+    ap.add_argument("--no-f64", action="store_true", help="skip the native-FP64 context measurement")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------------------
+# CPU oracle (bounded sample): the cpu_baseline leg and the --impl reference arm
+# ---------------------------------------------------------------------------------------------------------
+def oracle_sample_gates(gates, n):
+    """A fixed spread of the circuit's first layer: U(2) on low, middle and high qubits, and CNOTs."""
+    picks = [0, n // 2, n - 1, 5, 3 * n // 4, n // 4, n + 2, n + 7, 10, n - 5]
+    return [gates[i:i + 1] for i in picks if i < len(gates)]
+
+
+class OracleRunner:
+    def __init__(self, n, gates):
+        import oracle
+        self.oracle = oracle
+        self.threads = os.cpu_count() or 1
+        self.psi = oracle.basis_state(n, 0)
+        self.sample = oracle_sample_gates(gates, n)
+        self.i = 0
+
+    def step(self):
+        g = self.sample[self.i % len(self.sample)]
+        self.i += 1
+        self.oracle.apply_circuit(self.psi, g, threads=self.threads)
+
+    def desc(self, n):
+        return (f"single gates of the n={n} circuit's first layer (U(2) on qubits spread from 0 to n-1, and CNOTs), "
+                f"FP64 oracle (Algorithm 1 loop, outer loop over {self.threads} OpenMP threads), from |0...0>")
+
+
+def cpu_baseline(n, gates, budget_s):
+    r = OracleRunner(n, gates)
+    r.step()  # first touch of the 2^n-amplitude array outside the timing
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        r.step()
+        count += 1
+        if time.perf_counter() - t0 >= budget_s or count >= 200:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "gates/s", "cores": r.threads, "kind": "oracle",
+            "sample": f"{count} " + r.desc(n) + f"; {dt:.1f} s"}
+
+
+def run_reference(args):
+    if RANK != 0:
+        return
+    w = C.random_workload(args.n, args.depth, seed=SEED)
+    r = OracleRunner(args.n, w.gates)
+    for _ in range(max(args.warmup, 1)):
+        r.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.step()
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": f"gates/s, n={args.n} random circuit ({args.depth} layers), complex128",
+        "value": value, "unit": "gates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": r.threads, "kind": "oracle",
+                         "sample": f"each step = 1 " + r.desc(args.n)},
+        "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"random circuit, n={args.n} qubits, {args.depth} layers of Haar U(2) on every qubit + "
+                        f"CNOTs on a random perfect matching ({args.depth * (args.n + args.n // 2)} gates), "
+                        f"from |0...0>, seed {SEED}; then FP64 norm and {READ_COUNT} amplitudes read back",
+            "n": args.n, "layers": args.depth, "gates": args.depth * (args.n + args.n // 2),
+            "state_bytes_c128": 16 << args.n, "l2": "state larger than L2 (126 MB): no flush needed",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------------------------------------
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_ours(args):
+    import torch
+    from paper_1801_01037_gb300 import build as sv_build
+    dist = None
+    if WORLD > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+        dist = td
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    B.load()
+    torch.cuda.init()
+    w = C.random_workload(args.n, args.depth, seed=SEED)
+    gates = w.gates
+    G = len(gates)
+
+    def step(h, graph=True):
+        B.sv_init_basis(h, 0)
+        (B.sv_apply_circuit_graph if graph else B.sv_apply_circuit)(h, gates)
+        nrm = B.sv_norm(h)
+        amps = B.sv_read_amplitudes(h, 0, READ_COUNT)
+        return nrm, amps
+
+    def timed(dtype, arith, steps, warmup, profile=False, sampler=None):
+        h = B.sv_create(args.n, dtype)
+        try:
+            if dtype == B.SV_C128:
+                B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            B.sv_set_option(h, B.SV_OPT_PROFILE, 1 if profile else 0)
+            for _ in range(warmup):
+                step(h)
+            torch.cuda.synchronize()
+            barrier(dist)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fused_launches, fused_ms = 0, 0.0
+            if sampler:
+                sampler.start()
+            e0.record()
+            for _ in range(steps):
+                nrm, _ = step(h)
+                if profile:
+                    l, ms = B.sv_profile_last(h, 0)
+                    fused_launches += l
+                    fused_ms += ms
+            e1.record()
+            torch.cuda.synchronize()
+            clocks = sampler.stop() if sampler else None
+            barrier(dist)
+            ms = e0.elapsed_time(e1)
+            stats = B.sv_last_plan_stats(h)
+            return {"ms": ms, "norm": nrm, "fused_launches": fused_launches, "fused_ms": fused_ms, "stats": stats,
+                    "clocks": clocks}
+        finally:
+            B.sv_destroy(h)
+
+    sampler = ClockSampler()
+    c128 = timed(B.SV_C128, B.SV_ARITH_DF32, args.steps, args.warmup, profile=True, sampler=sampler)
+    c64 = timed(B.SV_C64, B.SV_ARITH_AUTO, args.steps, args.warmup)
+    f64 = None if args.no_f64 else timed(B.SV_C128, B.SV_ARITH_F64, 1, 1)
+
+    # end to end through the public API with host buffers: gate records uploaded and results read every step
+    h = B.sv_create(args.n, B.SV_C128)
+    try:
+        for _ in range(max(1, args.warmup)):
+            step(h, graph=False)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(h, graph=False)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        st = B.sv_last_plan_stats(h)
+    finally:
+        B.sv_destroy(h)
+
+    t_max = max_over_ranks(dist, c128["ms"]) / 1e3
+    total_gates = sum_over_ranks(dist, G * args.steps)
+    value = total_gates / t_max
+    e2e_max = max_over_ranks(dist, e2e_s)
+    e2e_value = total_gates / e2e_max
+    c64_t = max_over_ranks(dist, c64["ms"]) / 1e3
+    state_bytes = 16 << args.n
+
+    peak, peak_kind = measured_peaks()
+    avg_ms = c128["fused_ms"] / max(1, c128["fused_launches"])
+    achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9 if c128["fused_launches"] else None
+    traffic = committed_traffic()
+    launches_per_step = 1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
+    cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
+
+    if RANK != 0:
+        return
+    line = {
+        "metric": f"gates/s, n={args.n} random circuit ({args.depth} layers), complex128",
+        "value": value,
+        "unit": "gates/s",
+        "n_gpus": WORLD,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32x2 (double-float) arithmetic on IEEE-double complex128 storage",
+        "data": "synthetic (seeded Haar-random U(2) layers and random-matching CNOTs)",
+        "config": workload_config(args),
+        "effective_hbm_gbs": value * 2 * state_bytes / 1e9 / WORLD,
+        "c64": {"value": total_gates / c64_t, "unit": "gates/s",
+                "ms_per_step": c64_t * 1e3 / args.steps,
+                "effective_hbm_gbs": G * args.steps / c64_t * 2 * (8 << args.n) / 1e9},
+        "f64_native": None if f64 is None else {"value": G / (f64["ms"] / 1e3), "unit": "gates/s",
+                                                 "ms_per_step": f64["ms"], "note": "c128 with FP64 arithmetic, 1 step"},
+        "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
+                 "fused_gates_per_step": c128["stats"]["fused_gates"]},
+        "roofline": {"kernel": "k_fused<c128 df32> (fused chunk pass)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": 2 * state_bytes, "avg_launch_ms": avg_ms,
+                     "launches_timed": c128["fused_launches"], "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "gates/s",
+                "h2d_bytes_per_step": st["fused_gates"] * 192 + st["sweep_gates"] * 0,
+                "d2h_bytes_per_step": 8 + READ_COUNT * 16},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": c128["clocks"],
+        "norm_last_step": c128["norm"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the fused c128 pass from the committed ncu summary, if it still matches the
+    kernel source (null otherwise)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fused_c128_df32_traffic.txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split() if "=" in line)
+        h = hashlib.sha256()
+        for f in ("sv_fused.cu", "sv_arith.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1801_01037_gb300", "csrc", f), "rb").read())
+        if kv.get("source_sha256") != h.hexdigest()[:16]:
+            return None
+        return float(kv["bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * sv.h -- C ABI of the GB300 state-vector simulator.
+ *
+ * The library stores only the 2^n amplitudes of an n-qubit state and applies each single-qubit gate,
+ * optionally controlled, to every amplitude pair whose indices differ in the target bit: the state-vector
+ * method of LaRose, "Distributed Memory Techniques for Classical Simulation of Quantum Circuits"
+ * (arXiv:1801.01037), Sec. V.A (the strided pair-update equation) and Sec. V.B (Algorithm 1 and its
+ * controlled variant).
+ *
+ * Conventions shared by every entry point
+ *   - Qubit t is bit t of the amplitude index (the paper's stride rule: qubit i pairs k with k + 2^i,
+ *     Sec. V.A, Fig. "statevector").  Index k of a logical read is the integer sum_t b_t 2^t.
+ *   - Amplitudes are interleaved complex numbers: SV_C128 = two IEEE doubles (16 B), SV_C64 = two floats (8 B).
+ *   - Gate matrices are always given in double precision, row-major (q11, q12, q21, q22) as (re, im) pairs.
+ *   - Every call returns an sv_status.  Arguments are validated on the host before any device work; on an
+ *     error nothing is launched and sv_last_error() describes the problem.  No call aborts or throws.
+ *   - A state handle is not thread-safe; its work is ordered on the CUDA stream given at creation
+ *     (NULL = the legacy default stream).  Calls that return data to the host synchronise that stream.
+ *   - Pointers named host_* are host memory; dev_ptr arguments are device memory of the current device.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sv_status;
+#define SV_OK 0
+#define SV_ERR_ARG (-1)          /* bad argument: NULL pointer, qubit out of range, duplicate qubits, ... */
+#define SV_ERR_OOM (-2)          /* device (or pinned host) allocation failed, or over the server budget */
+#define SV_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define SV_ERR_NOT_UNITARY (-4)  /* max |U^dagger U - I| > 1e-10 */
+#define SV_ERR_TIMEOUT (-5)      /* a bounded device or host wait ran out */
+#define SV_ERR_BUSY (-6)         /* the server cannot take the request now (queue full) */
+#define SV_ERR_NOT_FOUND (-7)    /* unknown ticket */
+#define SV_ERR_NO_DEVICE (-8)    /* no CUDA device, or not an sm_103 device */
+
+typedef enum { SV_C64 = 1, SV_C128 = 2 } sv_dtype;
+
+/* Arithmetic used for complex128 states.  The storage stays IEEE double in every mode.
+ *   SV_ARITH_AUTO  : SV_ARITH_DF32 for complex128, FP32 for complex64 (the default).
+ *   SV_ARITH_F64   : native FP64 multiply-adds (exact IEEE double, about 1/70 of the FP32 rate on GB300).
+ *   SV_ARITH_DF32  : each double is split into a pair of floats (hi + lo, >= 47 significant bits) with
+ *                    integer bit operations, the 2x2 product is a compensated float dot product, and the
+ *                    result is re-assembled into a double; relative error per gate <= 2^-44.
+ * complex64 states always use FP32 arithmetic. */
+typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_F64 = 1, SV_ARITH_DF32 = 2 } sv_arith;
+
+#define SV_MAX_CONTROLS 4
+#define SV_GATE_U 0     /* 2x2 unitary on `target`, acting where every control bit is 1 (Sec. V.B) */
+#define SV_GATE_SWAP 1  /* exchange qubits `target` and `target2` (Sec. VI.B's relabelling) */
+
+/* One gate record, 96 bytes. */
+typedef struct sv_gate {
+    double U[8];                       /* q11, q12, q21, q22 as (re, im); ignored for SV_GATE_SWAP */
+    int32_t kind;                      /* SV_GATE_U or SV_GATE_SWAP */
+    int32_t target;                    /* target qubit, 0 <= target < n */
+    int32_t target2;                   /* second SWAP qubit; ignored (set -1) for SV_GATE_U */
+    int32_t ncontrols;                 /* 0..SV_MAX_CONTROLS */
+    int32_t controls[SV_MAX_CONTROLS]; /* distinct, != target, < n */
+} sv_gate;
+
+typedef struct sv_state sv_state;
+typedef struct sv_server sv_server;
+
+/* Options for sv_set_option. */
+#define SV_OPT_ARITH 1          /* sv_arith value */
+#define SV_OPT_CHUNK_QUBITS 2   /* k: 2^k amplitudes per fused chunk (0 = tuned default, else 6..13) */
+#define SV_OPT_FUSION 3         /* 1 = fuse gates into chunk passes (default), 0 = one sweep kernel per gate */
+#define SV_OPT_RENORM_PERIOD 4  /* renormalise every R applied gates (0 = never, the default) */
+#define SV_OPT_CANONICAL 5      /* 1 = restore logical bit order after every apply call (default for
+                                   sv_create_from_buffer states), 0 = keep the relabelled layout lazily */
+#define SV_OPT_PROFILE 6        /* 1 = record a CUDA event before and after every launch of the apply calls
+                                   (also inside captured graphs); read them with sv_profile_last */
+
+/* ---------------------------------------------------------------------------------------------------------
+ * States
+ * ------------------------------------------------------------------------------------------------------- */
+
+/* Allocate a 2^n-amplitude state in device memory (library-owned) and set it to |0...0> (Sec. II.A).
+ * n: 1 <= n <= 36 and the state must fit in free device memory.  stream: a cudaStream_t or NULL.
+ * Errors: SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_NO_DEVICE.  *out is set only on success. */
+sv_status sv_create(int n, sv_dtype dtype, void *stream, sv_state **out);
+
+/* Wrap caller-owned device memory of 2^n amplitudes (e.g. a torch tensor's storage); the contents are
+ * taken as the current state in logical order and are not modified here.  dev_ptr must be 16-byte
+ * aligned and stay valid until sv_destroy.  The library never frees it.  The buffer is kept in logical
+ * order after every call (SV_OPT_CANONICAL defaults to 1). */
+sv_status sv_create_from_buffer(int n, sv_dtype dtype, void *dev_ptr, void *stream, sv_state **out);
+
+/* Release the handle and, for sv_create states, the device memory.  NULL is accepted. */
+sv_status sv_destroy(sv_state *s);
+
+/* |x>: amplitude x = 1, all others 0.  x < 2^n.  Resets the layout to the identity. */
+sv_status sv_init_basis(sv_state *s, uint64_t x);
+
+/* Copy `count` amplitudes from host memory (state's dtype, logical order) into indices first..first+count-1
+ * (checkpoint restore). */
+sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const void *host_in);
+
+sv_status sv_set_option(sv_state *s, int option, int64_t value);
+sv_status sv_get_info(sv_state *s, int *n, sv_dtype *dtype, void **dev_ptr);
+
+/* Logical-to-physical qubit map: perm[t] = index bit that currently holds qubit t (the paper's
+ * non-sequential storage, Sec. VI.B).  perm must hold n ints. */
+sv_status sv_get_layout(sv_state *s, int *perm);
+
+/* Put the amplitudes back in logical order in device memory (perm = identity) with in-place bit-swap passes. */
+sv_status sv_canonicalize(sv_state *s);
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Gates (Sec. V.A pair update; Sec. V.B controlled variant)
+ * ------------------------------------------------------------------------------------------------------- */
+
+/* Apply the 2x2 unitary U on qubit `target`, restricted to indices whose `ncontrols` control bits are all 1.
+ * U: 8 doubles, row-major (re, im).  controls may be NULL when ncontrols == 0.
+ * Errors: SV_ERR_ARG (qubit out of range, control == target, duplicate controls, > SV_MAX_CONTROLS),
+ *         SV_ERR_NOT_UNITARY, SV_ERR_CUDA. */
+sv_status sv_apply_gate(sv_state *s, const double *U, int target, const int *controls, int ncontrols);
+
+/* SWAP of qubits a and b.  Done as a relabelling of the layout map (no data movement) unless the state is
+ * canonical-only (buffer states), where an in-place bit-swap pass runs. */
+sv_status sv_apply_swap(sv_state *s, int a, int b);
+
+/* Apply `ngates` gate records (host memory) in order.  All records are validated before any work; the
+ * planner fuses runs of gates into passes over 2^k-amplitude chunks.  Error: index of the first bad gate in
+ * sv_last_error(). */
+sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t ngates);
+
+/* Same as sv_apply_circuit, but the gate list is captured once into a CUDA graph keyed by its contents
+ * and the graph is replayed on later calls with identical gates and layout. */
+sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngates);
+
+/* Host-only dry run of the planner for `ngates` records on n qubits of `dtype` (chunk_k = 0: the default
+ * chunk size), starting from the identity layout.  No device work; works without a GPU.
+ *   *nsteps            number of launches the plan makes (fused passes and single-gate sweeps)
+ *   step_of_gate[i]    launch that applies gate i, or -1 for a SWAP folded into the layout / an identity
+ *   order_of_gate[i]   position of gate i in execution order (the planner reorders only commuting gates:
+ *                      gates that share a qubit keep their order)
+ *   step_qmask[j]      physical index bits spanned by launch j's chunks (a sweep: its target bit), j < max_steps
+ *   final_perm[t]      physical bit of logical qubit t after the circuit
+ * Array outputs may be NULL.  Errors: SV_ERR_ARG, SV_ERR_NOT_UNITARY (as sv_apply_circuit). */
+sv_status sv_plan_dry_run(int n, sv_dtype dtype, int chunk_k, const sv_gate *gates, size_t ngates, int *nsteps,
+                          int *step_of_gate, int *order_of_gate, uint64_t *step_qmask, int max_steps,
+                          int *final_perm);
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Read-out and reductions
+ * ------------------------------------------------------------------------------------------------------- */
+
+/* Copy amplitudes first..first+count-1 (logical order) to host memory in the state's dtype.  Synchronises. */
+sv_status sv_read_amplitudes(sv_state *s, uint64_t first, uint64_t count, void *host_out);
+
+/* Same, but gather the logical indices listed in host array `idx` (count entries, each < 2^n). */
+sv_status sv_read_amplitudes_at(sv_state *s, const uint64_t *idx, uint64_t count, void *host_out);
+
+/* |alpha_k|^2 (Sec. II.A) for k = first..first+count-1, in double precision, to host memory. */
+sv_status sv_read_probabilities(sv_state *s, uint64_t first, uint64_t count, double *host_out);
+
+/* sum_k |alpha_k|^2 accumulated in (at least) double precision.  Synchronises. */
+sv_status sv_norm(sv_state *s, double *out);
+
+/* Divide every amplitude by sqrt(sum |alpha_k|^2). */
+sv_status sv_renormalize(sv_state *s);
+
+/* Wait for all queued work of the state. */
+sv_status sv_sync(sv_state *s);
+
+/* Planner statistics of the last apply call: passes launched, gates applied inside fused passes, gates
+ * applied by single-gate sweeps, SWAPs folded into the layout, bit-swap passes.  Any pointer may be NULL. */
+sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
+                             int *remaps);
+
+/* With SV_OPT_PROFILE on: device time of the launches of the most recent apply call (or graph replay) of one
+ * kind (0 = fused chunk pass, 1 = single-gate sweep, 2 = bit-swap pass), summed over its launches.  Waits for
+ * those launches.  *launches = 0 when profiling is off or nothing of that kind ran. */
+sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms);
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Batches and serving
+ * ------------------------------------------------------------------------------------------------------- */
+
+/* Run `count` independent circuits, circuit i on a fresh |0...0> state of n[i] qubits, all of one dtype,
+ * with their passes interleaved in shared launches on `stream`.  out[i] receives a new library-owned
+ * state (destroy each with sv_destroy).  Errors leave out[] untouched. */
+sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
+                       const size_t *ngates, void *stream, sv_state **out);
+
+/* A serving loop on its own host thread and stream: admits requests while their states fit in
+ * hbm_budget_bytes and fewer than max_active run, and advances every admitted request by one pass per
+ * iteration (continuous batching: requests join and leave between iterations). */
+sv_status sv_server_create(size_t hbm_budget_bytes, int max_active, sv_server **out);
+sv_status sv_server_destroy(sv_server *srv);
+
+/* Queue a circuit on |0...0> of n qubits; the gates are copied.  SV_ERR_BUSY when the pending queue is
+ * full, SV_ERR_OOM when the state alone exceeds the budget. */
+sv_status sv_submit(sv_server *srv, int n, sv_dtype dtype, const sv_gate *gates, size_t ngates,
+                    uint64_t *ticket);
+
+/* Non-blocking: *done = 1 and *result = the final state (caller destroys it) once the request finished;
+ * *done = 0 otherwise.  A finished ticket can be polled successfully once. */
+sv_status sv_poll(sv_server *srv, uint64_t ticket, int *done, sv_state **result);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char *sv_last_error(void);
+
+/* Library version string. */
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_H */

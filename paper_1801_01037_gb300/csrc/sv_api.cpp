@@ -1,0 +1,464 @@
+// C ABI: handles, host-side validation, planning and launch of the kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sv_state.h"
+
+using namespace svi;
+
+namespace svi {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return set_error(SV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t amp_bytes(sv_dtype dt) { return dt == SV_C64 ? 8 : 16; }
+
+int mode_of(const sv_state *s) {
+  if (s->dtype == SV_C64) return MODE_C64_F32;
+  return s->arith == SV_ARITH_F64 ? MODE_C128_F64 : MODE_C128_DF32;
+}
+
+int check_device() {
+  static std::once_flag once;
+  static int status = SV_OK;
+  static std::string why;
+  std::call_once(once, [] {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+      status = SV_ERR_NO_DEVICE;
+      why = std::string("no CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "count = 0");
+      return;
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+      status = SV_ERR_NO_DEVICE;
+      why = "the kernels are built for sm_103a only; device is sm_" + std::to_string(major * 10 + minor);
+    }
+  });
+  if (status != SV_OK) return set_error(status, why);
+  return SV_OK;
+}
+
+PlanConfig plan_config(const sv_state *s) {
+  PlanConfig c;
+  if (s->dtype == SV_C64) { c.k = 13; c.c = 5; }
+  else { c.k = 12; c.c = 4; }
+  if (s->chunk_k > 0) c.k = s->chunk_k;
+  c.fusion = s->fusion != 0;
+  return c;
+}
+
+int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<DevGate> &b, DevGate **d_a,
+                 DevGate **d_b) {
+  const size_t total = a.size() + b.size();
+  *d_a = *d_b = nullptr;
+  if (total == 0) return SV_OK;
+  cudaError_t e;
+  if (s->stage_pending) {
+    if ((e = cudaEventSynchronize(s->stage_ev)) != cudaSuccess) return cuda_fail(e, "gate staging wait");
+    s->stage_pending = false;
+  }
+  if (total > s->d_gates_cap) {
+    if (s->d_gates) {
+      if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "stream sync");
+      cudaFree(s->d_gates);
+      s->d_gates = nullptr;
+    }
+    const size_t cap = std::max<size_t>(total, 256);
+    if ((e = cudaMalloc(&s->d_gates, cap * sizeof(DevGate))) != cudaSuccess) {
+      s->d_gates_cap = 0;
+      return set_error(SV_ERR_OOM, "device gate buffer allocation failed");
+    }
+    s->d_gates_cap = cap;
+  }
+  if (total > s->h_stage_cap) {
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->h_stage = nullptr;
+    const size_t cap = std::max<size_t>(total, 256);
+    if ((e = cudaMallocHost(&s->h_stage, cap * sizeof(DevGate))) != cudaSuccess) {
+      s->h_stage_cap = 0;
+      return set_error(SV_ERR_OOM, "pinned gate staging allocation failed");
+    }
+    s->h_stage_cap = cap;
+  }
+  if (!a.empty()) std::memcpy(s->h_stage, a.data(), a.size() * sizeof(DevGate));
+  if (!b.empty()) std::memcpy(s->h_stage + a.size(), b.data(), b.size() * sizeof(DevGate));
+  if ((e = cudaMemcpyAsync(s->d_gates, s->h_stage, total * sizeof(DevGate), cudaMemcpyHostToDevice, s->stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "gate upload");
+  if ((e = cudaEventRecord(s->stage_ev, s->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  s->stage_pending = true;
+  *d_a = s->d_gates;
+  *d_b = s->d_gates + a.size();
+  return SV_OK;
+}
+
+int maybe_renormalize(sv_state *s, int applied) {
+  if (s->renorm_period <= 0) return SV_OK;
+  s->gates_since_renorm += applied;
+  if (s->gates_since_renorm < s->renorm_period) return SV_OK;
+  s->gates_since_renorm = 0;
+  cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, s->d_scalars + norm_parts(), s->stream);
+  if (e == cudaSuccess) e = launch_scale(s->psi, s->n, mode_of(s), s->d_scalars + norm_parts(), s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "renormalise");
+}
+
+int ensure_event_pool(sv_state *s, size_t steps) {
+  while (s->ev_pool.size() < 2 * steps) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+    s->ev_pool.push_back(ev);
+  }
+  return SV_OK;
+}
+
+std::vector<int> step_kinds(const Plan &P) {
+  std::vector<int> k;
+  for (const Step &st : P.steps) k.push_back((int)st.kind);
+  return k;
+}
+
+int run_plan(sv_state *s, const Plan &P, DevGate *d_fused, DevGate *, cudaStream_t st, const cudaEvent_t *evs,
+             bool capturing) {
+  const int mode = mode_of(s);
+  const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  for (size_t si = 0; si < P.steps.size(); ++si) {
+    const Step &step = P.steps[si];
+    cudaError_t e = cudaSuccess;
+    if (evs && (e = cudaEventRecordWithFlags(evs[2 * si], st, rec_flags)) != cudaSuccess)
+      return cuda_fail(e, "profiling event");
+    if (step.kind == Step::FUSED) {
+      PassDesc d = P.passes[step.index];
+      d.psi = s->psi;
+      d.gates = d_fused + P.pass_gate_offset[step.index];
+      // A pass of pure exchanges (X / CNOT / Toffoli) moves doubles as they are: bit-exact in every mode.
+      bool moves_only = mode == MODE_C128_DF32;
+      for (int i = 0; moves_only && i < d.ngates; ++i)
+        moves_only = P.fused_gates[P.pass_gate_offset[step.index] + i].cls == GC_X;
+      e = launch_fused(d, moves_only ? (int)MODE_C128_F64 : mode, st);
+    } else if (step.kind == Step::SWEEP) {
+      e = launch_sweep(s->psi, s->n, mode, P.sweep_gates[step.index], st);
+    } else {
+      e = launch_remap_swap(s->psi, s->n, mode, step.a, step.b, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (evs && (e = cudaEventRecordWithFlags(evs[2 * si + 1], st, rec_flags)) != cudaSuccess)
+      return cuda_fail(e, "profiling event");
+    if (st == s->stream) {
+      const int rc = maybe_renormalize(s, step.ngates);
+      if (rc != SV_OK) return rc;
+    }
+  }
+  return SV_OK;
+}
+
+int canonicalize_now(sv_state *s) {
+  const auto swaps = canonicalize_steps(s->perm);
+  for (const auto &ab : swaps) {
+    cudaError_t e = launch_remap_swap(s->psi, s->n, mode_of(s), ab.first, ab.second, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bit-swap pass");
+  }
+  s->st_remaps += (int)swaps.size();
+  return SV_OK;
+}
+
+int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero) {
+  const size_t bytes = amp_bytes(dt) << n;
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+  if (bytes > free_b) return set_error(SV_ERR_OOM, "state of " + std::to_string(bytes) + " bytes exceeds free device memory");
+  sv_state *s = new sv_state();
+  s->n = n;
+  s->dtype = dt;
+  s->stream = st;
+  s->perm.resize(n);
+  for (int t = 0; t < n; ++t) s->perm[t] = t;
+  if ((e = cudaMalloc(&s->psi, bytes)) != cudaSuccess) {
+    delete s;
+    cudaGetLastError();
+    return set_error(SV_ERR_OOM, "cudaMalloc of the state failed");
+  }
+  if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    cudaFree(s->psi);
+    if (s->d_scalars) cudaFree(s->d_scalars);
+    delete s;
+    return cuda_fail(e, "state scratch allocation");
+  }
+  if (init_zero) {
+    if ((e = launch_init_basis(s->psi, n, mode_of(s), 0, st)) != cudaSuccess) {
+      sv_destroy(s);
+      return cuda_fail(e, "init");
+    }
+  }
+  *out = s;
+  return SV_OK;
+}
+
+} // namespace svi
+
+// =========================================================================================================
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+const char *sv_version(void) { return "gb300-statevec 0.1 (sm_103a)"; }
+
+static bool bad_dtype(sv_dtype dt) { return dt != SV_C64 && dt != SV_C128; }
+
+sv_status sv_create(int n, sv_dtype dtype, void *stream, sv_state **out) {
+  if (!out) return set_error(SV_ERR_ARG, "out is NULL");
+  if (n < 1 || n > kMaxQubits) return set_error(SV_ERR_ARG, "n must be in [1, 36]");
+  if (bad_dtype(dtype)) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+  int rc = check_device();
+  if (rc != SV_OK) return rc;
+  return alloc_state(n, dtype, (cudaStream_t)stream, out, true);
+}
+
+sv_status sv_create_from_buffer(int n, sv_dtype dtype, void *dev_ptr, void *stream, sv_state **out) {
+  if (!out || !dev_ptr) return set_error(SV_ERR_ARG, "out or dev_ptr is NULL");
+  if (n < 1 || n > kMaxQubits) return set_error(SV_ERR_ARG, "n must be in [1, 36]");
+  if (bad_dtype(dtype)) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+  if (((uintptr_t)dev_ptr & 15u) != 0) return set_error(SV_ERR_ARG, "dev_ptr must be 16-byte aligned");
+  int rc = check_device();
+  if (rc != SV_OK) return rc;
+  sv_state *s = new sv_state();
+  s->n = n;
+  s->dtype = dtype;
+  s->stream = (cudaStream_t)stream;
+  s->psi = dev_ptr;
+  s->owned = false;
+  s->canonical = 1;
+  s->perm.resize(n);
+  for (int t = 0; t < n; ++t) s->perm[t] = t;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    if (s->d_scalars) cudaFree(s->d_scalars);
+    delete s;
+    return cuda_fail(e, "state scratch allocation");
+  }
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_state *s) {
+  if (!s) return SV_OK;
+  cudaStreamSynchronize(s->stream);
+  for (auto &kv : s->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.d_gates) cudaFree(kv.second.d_gates);
+  }
+  if (s->owned && s->psi) cudaFree(s->psi);
+  if (s->d_gates) cudaFree(s->d_gates);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->d_scalars) cudaFree(s->d_scalars);
+  if (s->d_read) cudaFree(s->d_read);
+  if (s->stage_ev) cudaEventDestroy(s->stage_ev);
+  for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
+  for (auto &kv : s->graphs)
+    for (cudaEvent_t ev : kv.second.evs) cudaEventDestroy(ev);
+  delete s;
+  return SV_OK;
+}
+
+sv_status sv_init_basis(sv_state *s, uint64_t x) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  if (x >= (1ull << s->n)) return set_error(SV_ERR_ARG, "basis index out of range");
+  for (int t = 0; t < s->n; ++t) s->perm[t] = t;
+  s->gates_since_renorm = 0;
+  cudaError_t e = launch_init_basis(s->psi, s->n, mode_of(s), x, s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "init");
+}
+
+sv_status sv_set_option(sv_state *s, int option, int64_t value) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  switch (option) {
+    case SV_OPT_ARITH:
+      if (value != SV_ARITH_AUTO && value != SV_ARITH_F64 && value != SV_ARITH_DF32)
+        return set_error(SV_ERR_ARG, "bad arithmetic mode");
+      s->arith = (int)value;
+      return SV_OK;
+    case SV_OPT_CHUNK_QUBITS:
+      if (value != 0 && (value < 6 || value > kMaxChunkQubits)) return set_error(SV_ERR_ARG, "chunk qubits must be 0 or 6..13");
+      if (value > 12 && s->dtype == SV_C128) return set_error(SV_ERR_ARG, "complex128 chunks are at most 2^12 amplitudes");
+      s->chunk_k = (int)value;
+      return SV_OK;
+    case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
+    case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
+    case SV_OPT_RENORM_PERIOD:
+      if (value < 0) return set_error(SV_ERR_ARG, "renormalisation period must be >= 0");
+      s->renorm_period = value;
+      return SV_OK;
+    case SV_OPT_CANONICAL:
+      if (!s->owned && !value) return set_error(SV_ERR_ARG, "buffer states stay in logical order");
+      s->canonical = value ? 1 : 0;
+      return SV_OK;
+    default: return set_error(SV_ERR_ARG, "unknown option");
+  }
+}
+
+sv_status sv_get_info(sv_state *s, int *n, sv_dtype *dtype, void **dev_ptr) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  if (n) *n = s->n;
+  if (dtype) *dtype = s->dtype;
+  if (dev_ptr) *dev_ptr = s->psi;
+  return SV_OK;
+}
+
+sv_status sv_get_layout(sv_state *s, int *perm) {
+  if (!s || !perm) return set_error(SV_ERR_ARG, "NULL argument");
+  for (int t = 0; t < s->n; ++t) perm[t] = s->perm[t];
+  return SV_OK;
+}
+
+sv_status sv_canonicalize(sv_state *s) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  return canonicalize_now(s);
+}
+
+static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool single) {
+  for (size_t i = 0; i < ngates; ++i) {
+    std::string why;
+    const int rc = validate_gate(gates[i], s->n, why);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+  }
+  PlanConfig cfg = plan_config(s);
+  if (single) cfg.fusion = false;
+  Plan P;
+  make_plan(s->n, cfg, s->perm, gates, ngates, P);
+  DevGate *d_fused = nullptr, *d_sweep = nullptr;
+  int rc = upload_gates(s, P.fused_gates, {}, &d_fused, &d_sweep);
+  if (rc != SV_OK) return rc;
+  const cudaEvent_t *evs = nullptr;
+  s->last_evs = nullptr;
+  s->last_kind.clear();
+  if (s->profile) {
+    if ((rc = ensure_event_pool(s, P.steps.size())) != SV_OK) return rc;
+    evs = s->ev_pool.data();
+    s->last_evs = evs;
+    s->last_kind = step_kinds(P);
+  }
+  rc = run_plan(s, P, d_fused, d_sweep, s->stream, evs, false);
+  if (rc != SV_OK) return rc;
+  s->st_passes = (int)P.passes.size();
+  s->st_fused = P.n_fused_gates;
+  s->st_sweeps = P.n_sweep_gates;
+  s->st_relabels = P.n_relabels;
+  s->st_remaps = 0;
+  if (s->canonical) return canonicalize_now(s);
+  return SV_OK;
+}
+
+sv_status sv_apply_gate(sv_state *s, const double *U, int target, const int *controls, int ncontrols) {
+  if (!s || !U) return set_error(SV_ERR_ARG, "NULL argument");
+  if (ncontrols < 0 || ncontrols > SV_MAX_CONTROLS) return set_error(SV_ERR_ARG, "ncontrols out of range");
+  if (ncontrols > 0 && !controls) return set_error(SV_ERR_ARG, "controls is NULL");
+  sv_gate g;
+  std::memset(&g, 0, sizeof g);
+  std::memcpy(g.U, U, sizeof g.U);
+  g.kind = SV_GATE_U;
+  g.target = target;
+  g.target2 = -1;
+  g.ncontrols = ncontrols;
+  for (int i = 0; i < SV_MAX_CONTROLS; ++i) g.controls[i] = i < ncontrols ? controls[i] : -1;
+  return apply_records(s, &g, 1, true);
+}
+
+sv_status sv_apply_swap(sv_state *s, int a, int b) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  sv_gate g;
+  std::memset(&g, 0, sizeof g);
+  g.kind = SV_GATE_SWAP;
+  g.target = a;
+  g.target2 = b;
+  return apply_records(s, &g, 1, true);
+}
+
+sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t ngates) {
+  if (!s || (!gates && ngates)) return set_error(SV_ERR_ARG, "NULL argument");
+  return apply_records(s, gates, ngates, false);
+}
+
+sv_status sv_plan_dry_run(int n, sv_dtype dtype, int chunk_k, const sv_gate *gates, size_t ngates, int *nsteps,
+                          int *step_of_gate, int *order_of_gate, uint64_t *step_qmask, int max_steps,
+                          int *final_perm) {
+  if (n < 1 || n > kMaxQubits) return set_error(SV_ERR_ARG, "n must be in [1, 36]");
+  if (bad_dtype(dtype)) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+  if (!gates && ngates) return set_error(SV_ERR_ARG, "gates is NULL");
+  for (size_t i = 0; i < ngates; ++i) {
+    std::string why;
+    const int rc = validate_gate(gates[i], n, why);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+  }
+  sv_state tmp;
+  tmp.n = n;
+  tmp.dtype = dtype;
+  tmp.chunk_k = chunk_k;
+  std::vector<int> perm(n);
+  for (int t = 0; t < n; ++t) perm[t] = t;
+  Plan P;
+  make_plan(n, plan_config(&tmp), perm, gates, ngates, P);
+  if (nsteps) *nsteps = (int)P.steps.size();
+  for (size_t i = 0; i < ngates; ++i) {
+    if (step_of_gate) step_of_gate[i] = P.gate_step[i];
+    if (order_of_gate) order_of_gate[i] = P.gate_order[i];
+  }
+  if (step_qmask)
+    for (int j = 0; j < max_steps && j < (int)P.step_qmask.size(); ++j) step_qmask[j] = P.step_qmask[j];
+  if (final_perm)
+    for (int t = 0; t < n; ++t) final_perm[t] = perm[t];
+  return SV_OK;
+}
+
+sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms) {
+  if (!s || !launches || !ms) return set_error(SV_ERR_ARG, "NULL argument");
+  *launches = 0;
+  *ms = 0.0;
+  if (!s->last_evs) return SV_OK;
+  for (size_t i = 0; i < s->last_kind.size(); ++i) {
+    if (s->last_kind[i] != kind) continue;
+    cudaError_t e = cudaEventSynchronize(s->last_evs[2 * i + 1]);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, s->last_evs[2 * i], s->last_evs[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+    ++*launches;
+    *ms += t;
+  }
+  return SV_OK;
+}
+
+sv_status sv_sync(sv_state *s) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "stream sync");
+}
+
+sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels, int *remaps) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  if (passes) *passes = s->st_passes;
+  if (fused_gates) *fused_gates = s->st_fused;
+  if (sweep_gates) *sweep_gates = s->st_sweeps;
+  if (relabels) *relabels = s->st_relabels;
+  if (remaps) *remaps = s->st_remaps;
+  return SV_OK;
+}
+
+} // extern "C"

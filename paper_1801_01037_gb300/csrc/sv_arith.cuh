@@ -1,0 +1,219 @@
+// Arithmetic of the three storage/arithmetic modes, as device functions on one amplitude.
+//
+// The update itself is the paper's strided pair update (Sec. V.A):
+//     a <- q11 a + q12 b,   b <- q21 a + q22 b      (a = alpha_k, b = alpha_{k + 2^t}, old values on the right)
+// written out per mode.  GB300 executes FP64 at about 1.7 fused multiply-adds per clock per SM and converts
+// double <-> float at the same rate, against about 120 FP32 multiply-adds per clock per SM, so complex128 is
+// by default computed in "double-float" (DF32) form: every double is split into an unevaluated float pair
+// hi + lo with integer bit operations only, the 2x2 complex product becomes four compensated float dot
+// products (exact products via FMA, exact sums via TwoSum, Dekker/Knuth), and the pair is re-assembled into
+// a double with integer operations, one float multiply and one float-to-int conversion.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "sv_internal.h"
+
+namespace svi {
+
+// ------------------------------------------------------------------------------------------------------
+// Double-float primitives
+// ------------------------------------------------------------------------------------------------------
+struct dfv { float h, l; };
+
+// x (IEEE double) -> hi + lo.  hi = x truncated to 24 significant bits, lo = the remaining 29 mantissa bits
+// rounded to 24 bits; |x - (hi + lo)| <= 2^-47 |x|.  Integer and float ops only (no FP64 instruction).
+// |x| < 2^-126 gives 0 (absolute error < 1.2e-38); the lo part is dropped for |x| < 2^-74.  Valid for
+// |x| < 2^128, which every amplitude of a normalised state satisfies.
+__device__ __forceinline__ dfv df_split(double x) {
+  const uint32_t lo = (uint32_t)__double2loint(x);
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t eh = hi & 0x7FF00000u;                 // biased exponent e << 20
+  const uint32_t t = __funnelshift_l(lo, hi, 3);        // top 23 mantissa bits in t[22:0]
+  const uint32_t hb = (t & 0x007FFFFFu) | (eh * 8u - (896u << 23));   // float exponent e - 1023 + 127
+  const float rf = __uint2float_rn(lo & 0x1FFFFFFFu);   // residual mantissa bits as an integer
+  const float sc = __uint_as_float(eh * 8u - (948u << 23));            // 2^(e - 1075)
+  const float l = __fmul_rn(rf, sc);
+  dfv r;
+  r.h = (eh >= (897u << 20)) ? __uint_as_float(hb | sign) : 0.0f;
+  r.l = (eh >= (949u << 20)) ? __uint_as_float(__float_as_uint(l) | sign) : 0.0f;
+  return r;
+}
+
+// s + e -> nearest double, for |e| <= ulp(s)/2 (as TwoSum leaves it).  The double's bit pattern is s's bits
+// re-biased, plus e measured in units of the double ulp of s's binade (|delta| <= 2^28, so an int32).
+// When s is a power of two and the correction lowers |s|, the result lies in the binade below, whose ulp
+// is half as large, so delta doubles.  Float zero or subnormal s gives (signed) zero.
+__device__ __forceinline__ double df_combine(float s, float e) {
+  const uint32_t sb = __float_as_uint(s);
+  const uint32_t sign = sb & 0x80000000u;
+  const uint32_t mag = sb & 0x7FFFFFFFu;
+  const uint32_t fexp = mag & 0x7F800000u;
+  const uint32_t dhi = ((mag >> 3) + (896u << 20)) | sign;
+  const uint32_t dlo = mag << 29;
+  const float scale = __uint_as_float(((306u << 23) - fexp) | sign);  // +-2^(52 - (exp(s) - 127))
+  int32_t delta = __float2int_rn(__fmul_rn(e, scale));
+  if ((mag & 0x007FFFFFu) == 0u && delta < 0) delta *= 2;
+  delta = (fexp >= (53u << 23)) ? delta : 0;
+  uint64_t bits = (((uint64_t)dhi) << 32 | dlo) + (uint64_t)(int64_t)delta;
+  bits = (fexp == 0u) ? (((uint64_t)sign) << 32) : bits;
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (qh + ql)(xh + xl): returns the rounded product qh*xh and adds its exact rounding error plus the two
+// cross terms to c (the ql*xl term is below 2^-48 relative and dropped).
+__device__ __forceinline__ float df_prod(float qh, float ql, dfv x, float &c) {
+  const float p = __fmul_rn(qh, x.h);
+  c = __fadd_rn(c, __fmaf_rn(qh, x.h, -p));
+  c = __fmaf_rn(qh, x.l, c);
+  c = __fmaf_rn(ql, x.h, c);
+  return p;
+}
+
+// sum of four double-float products, renormalised with TwoSum.
+__device__ __forceinline__ dfv df_dot4(float q0h, float q0l, dfv x0, float q1h, float q1l, dfv x1,
+                                       float q2h, float q2l, dfv x2, float q3h, float q3l, dfv x3) {
+  float c = 0.0f, s, e;
+  const float p0 = df_prod(q0h, q0l, x0, c);
+  const float p1 = df_prod(q1h, q1l, x1, c);
+  const float p2 = df_prod(q2h, q2l, x2, c);
+  const float p3 = df_prod(q3h, q3l, x3, c);
+  two_sum(p0, p1, s, e); c = __fadd_rn(c, e);
+  two_sum(s, p2, s, e); c = __fadd_rn(c, e);
+  two_sum(s, p3, s, e); c = __fadd_rn(c, e);
+  dfv r;
+  two_sum(s, c, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ dfv df_dot2(float q0h, float q0l, dfv x0, float q1h, float q1l, dfv x1) {
+  float c = 0.0f, s, e;
+  const float p0 = df_prod(q0h, q0l, x0, c);
+  const float p1 = df_prod(q1h, q1l, x1, c);
+  two_sum(p0, p1, s, e); c = __fadd_rn(c, e);
+  dfv r;
+  two_sum(s, c, r.h, r.l);
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Per-mode amplitude types.  G: element in global memory.  S: working form in registers / shared memory.
+// ------------------------------------------------------------------------------------------------------
+template <int MODE> struct Arith;
+
+// Coefficients of one gate in the working precision of a mode, loaded once per gate.
+struct CoefF32 { float q[8]; };
+struct CoefF64 { double q[8]; };
+struct CoefDF { float h[8], l[8]; };
+
+template <> struct Arith<MODE_C64_F32> {
+  using G = float2;
+  using S = float2;
+  using Coef = CoefF32;
+  static __device__ __forceinline__ S load(G v) { return v; }
+  static __device__ __forceinline__ G store(S v) { return v; }
+  static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ S one() { return make_float2(1.f, 0.f); }
+  static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c.q[i] = g.qf[i];
+  }
+  // r = q[j] * a   (q[j] = complex entry j of the matrix: 0 = q11, 1 = q12, 2 = q21, 3 = q22)
+  static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
+    const float qr = c.q[2 * j], qi = c.q[2 * j + 1];
+    return make_float2(__fmaf_rn(qr, a.x, -qi * a.y), __fmaf_rn(qr, a.y, qi * a.x));
+  }
+  static __device__ __forceinline__ void pair(const Coef &c, S &a, S &b) {
+    const float *q = c.q;
+    S r0, r1;
+    r0.x = __fmaf_rn(q[0], a.x, __fmaf_rn(-q[1], a.y, __fmaf_rn(q[2], b.x, -q[3] * b.y)));
+    r0.y = __fmaf_rn(q[0], a.y, __fmaf_rn(q[1], a.x, __fmaf_rn(q[2], b.y, q[3] * b.x)));
+    r1.x = __fmaf_rn(q[4], a.x, __fmaf_rn(-q[5], a.y, __fmaf_rn(q[6], b.x, -q[7] * b.y)));
+    r1.y = __fmaf_rn(q[4], a.y, __fmaf_rn(q[5], a.x, __fmaf_rn(q[6], b.y, q[7] * b.x)));
+    a = r0; b = r1;
+  }
+};
+
+template <> struct Arith<MODE_C128_F64> {
+  using G = double2;
+  using S = double2;
+  using Coef = CoefF64;
+  static __device__ __forceinline__ S load(G v) { return v; }
+  static __device__ __forceinline__ G store(S v) { return v; }
+  static __device__ __forceinline__ S zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ S one() { return make_double2(1.0, 0.0); }
+  static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c.q[i] = g.q[i];
+  }
+  static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
+    const double qr = c.q[2 * j], qi = c.q[2 * j + 1];
+    return make_double2(__fma_rn(qr, a.x, -qi * a.y), __fma_rn(qr, a.y, qi * a.x));
+  }
+  static __device__ __forceinline__ void pair(const Coef &c, S &a, S &b) {
+    const double *q = c.q;
+    S r0, r1;
+    r0.x = __fma_rn(q[0], a.x, __fma_rn(-q[1], a.y, __fma_rn(q[2], b.x, -q[3] * b.y)));
+    r0.y = __fma_rn(q[0], a.y, __fma_rn(q[1], a.x, __fma_rn(q[2], b.y, q[3] * b.x)));
+    r1.x = __fma_rn(q[4], a.x, __fma_rn(-q[5], a.y, __fma_rn(q[6], b.x, -q[7] * b.y)));
+    r1.y = __fma_rn(q[4], a.y, __fma_rn(q[5], a.x, __fma_rn(q[6], b.y, q[7] * b.x)));
+    a = r0; b = r1;
+  }
+};
+
+// Working form of a DF32 amplitude: (re.hi, re.lo, im.hi, im.lo).
+template <> struct Arith<MODE_C128_DF32> {
+  using G = double2;
+  using S = float4;
+  using Coef = CoefDF;
+  static __device__ __forceinline__ S load(G v) {
+    const dfv r = df_split(v.x), i = df_split(v.y);
+    return make_float4(r.h, r.l, i.h, i.l);
+  }
+  static __device__ __forceinline__ G store(S v) { return make_double2(df_combine(v.x, v.y), df_combine(v.z, v.w)); }
+  static __device__ __forceinline__ S zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ S one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { c.h[i] = g.qh[i]; c.l[i] = g.ql[i]; }
+  }
+  static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
+    const dfv ar{a.x, a.y}, ai{a.z, a.w};
+    const float rh = c.h[2 * j], rl = c.l[2 * j], ih = c.h[2 * j + 1], il = c.l[2 * j + 1];
+    const dfv xr = df_dot2(rh, rl, ar, -ih, -il, ai);
+    const dfv xi = df_dot2(rh, rl, ai, ih, il, ar);
+    return make_float4(xr.h, xr.l, xi.h, xi.l);
+  }
+  static __device__ __forceinline__ void pair(const Coef &c, S &a, S &b) {
+    const dfv ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+    const float *h = c.h, *l = c.l;
+    const dfv o0r = df_dot4(h[0], l[0], ar, -h[1], -l[1], ai, h[2], l[2], br, -h[3], -l[3], bi);
+    const dfv o0i = df_dot4(h[0], l[0], ai, h[1], l[1], ar, h[2], l[2], bi, h[3], l[3], br);
+    const dfv o1r = df_dot4(h[4], l[4], ar, -h[5], -l[5], ai, h[6], l[6], br, -h[7], -l[7], bi);
+    const dfv o1i = df_dot4(h[4], l[4], ai, h[5], l[5], ar, h[6], l[6], bi, h[7], l[7], br);
+    a = make_float4(o0r.h, o0r.l, o0i.h, o0i.l);
+    b = make_float4(o1r.h, o1r.l, o1i.h, o1i.l);
+  }
+};
+
+// Apply one gate class to an amplitude pair (a = target bit 0, b = target bit 1).
+template <int MODE>
+__device__ __forceinline__ void apply_pair(uint32_t cls, const typename Arith<MODE>::Coef &c,
+                                           typename Arith<MODE>::S &a, typename Arith<MODE>::S &b) {
+  using M = Arith<MODE>;
+  switch (cls) {
+    case GC_GENERAL: M::pair(c, a, b); break;
+    case GC_DIAG: a = M::cmul(c, 0, a); b = M::cmul(c, 3, b); break;
+    case GC_PHASE: b = M::cmul(c, 3, b); break;
+    case GC_ANTIDIAG: { const auto t = M::cmul(c, 1, b); b = M::cmul(c, 2, a); a = t; } break;
+    default: { const auto t = a; a = b; b = t; } break;  // GC_X
+  }
+}
+
+} // namespace svi

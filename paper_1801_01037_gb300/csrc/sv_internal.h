@@ -1,0 +1,88 @@
+// Internal structures shared by the host runtime (C++) and the CUDA kernels.  Not part of the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace svi {
+
+constexpr int kMaxQubits = 36;
+constexpr int kMaxChunkQubits = 13;
+
+// Storage / arithmetic modes.  The storage of C128 is IEEE double in every mode.
+enum Mode : int {
+  MODE_C64_F32 = 0,   // complex64 storage, FP32 arithmetic
+  MODE_C128_F64 = 1,  // complex128 storage, native FP64 arithmetic
+  MODE_C128_DF32 = 2, // complex128 storage, double-float (hi+lo float pair) arithmetic
+};
+
+// Gate classes, decided on the host by exact comparisons of the FP64 matrix entries.
+enum GateClass : uint32_t {
+  GC_GENERAL = 0,   // dense 2x2
+  GC_DIAG = 1,      // q12 = q21 = 0: each amplitude scaled by q11 or q22, no pairing
+  GC_PHASE = 2,     // diagonal with q11 = 1: only amplitudes whose target bit is 1 change
+  GC_ANTIDIAG = 3,  // q11 = q22 = 0: alpha_k <- q12 alpha_{k+2^t}, alpha_{k+2^t} <- q21 alpha_k
+  GC_X = 4,         // q12 = q21 = 1, q11 = q22 = 0: the pair is exchanged (pure moves)
+};
+
+// One gate as the kernels see it.  In a single-gate sweep, `target` and `cmask` are physical bits.  Inside
+// a fused pass they are chunk-local bits; controls that lie outside the chunk go to `gmask` (physical bits
+// that must all be 1 in the chunk's base index), and a diagonal gate whose target lies outside the chunk
+// has target = -1 and its physical target bit in `tmask`.
+struct DevGate {
+  double q[8];       // q11, q12, q21, q22 (re, im), FP64
+  float qf[8];       // the same rounded to float (complex64 arithmetic)
+  float qh[8];       // double-float split: q = qh + ql
+  float ql[8];
+  uint64_t cmask;
+  uint64_t gmask;
+  uint64_t tmask;
+  int32_t target;
+  uint32_t cls;
+};
+static_assert(sizeof(DevGate) == 192, "DevGate layout");
+
+// One fused pass over all chunks of a state.  A chunk is the 2^k amplitudes whose indices agree outside
+// the physical bits qpos[0..k-1]; qpos[j] = j for j < c, so each chunk is 2^(k-c) runs of 2^c contiguous
+// amplitudes.  On store, chunk-local bit j goes to physical bit qpos_out[j] (a permutation of qpos over the
+// same set of bits, so every chunk writes exactly the addresses it read: the pass stays in place).
+struct PassDesc {
+  void *psi;
+  const DevGate *gates;   // device array, ngates entries
+  uint64_t qmask;         // OR of 1 << qpos[j]
+  uint64_t init_x;        // with init = 1: the pass starts from the basis state |init_x> (physical index)
+  int32_t n, k, c, ngates;
+  int8_t qpos[16];        // ascending; qpos[j] = j for j < c
+  int8_t qpos_out[16];
+  int32_t init;           // 0: read the chunk from HBM; 1: synthesise |init_x> restricted to the chunk
+  int32_t permuted;       // 1 if qpos_out differs from qpos
+};
+static_assert(sizeof(PassDesc) == 88, "PassDesc layout");
+
+// ---------------------------------------------------------------------------------------------------------
+// Kernel launchers (sv_kernels.cu).  All return cudaGetLastError() of the launch.
+// ---------------------------------------------------------------------------------------------------------
+cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream_t st);
+cudaError_t launch_sweep(void *psi, int n, int mode, const DevGate &g, cudaStream_t st);
+cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st);
+int fused_smem_bytes(int mode, int k);
+cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st);
+// Logical-order gather: out[i] = psi[phys(idx_i)], idx_i = first + i (d_idx == nullptr) or d_idx[i].
+// perm[t] = physical bit of logical qubit t.
+cudaError_t launch_gather(const void *psi, int n, int mode, const int *perm, uint64_t first, uint64_t count,
+                          const uint64_t *d_idx, void *d_out, cudaStream_t st);
+cudaError_t launch_probs(const void *psi, int n, int mode, const int *perm, uint64_t first, uint64_t count,
+                         double *d_out, cudaStream_t st);
+// Sum of |psi_k|^2: stage 1 writes `nparts` partial sums (as double) to d_partials, stage 2 adds them in a
+// fixed order into *d_out.  nparts must be norm_parts().
+int norm_parts();
+cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st);
+cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cudaStream_t st);
+
+// Batched fused pass: `npass` pass descriptors in device memory; block b handles chunk b - chunk_start[p]
+// of pass p, where chunk_start is an exclusive prefix sum over the passes' chunk counts (device array of
+// npass + 1 entries).  All passes share `mode`; each has its own k <= kmax (shared memory is sized for kmax).
+cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass,
+                               uint64_t total_chunks, int mode, int kmax, cudaStream_t st);
+
+} // namespace svi

@@ -1,0 +1,334 @@
+// CUDA kernels for sm_103a: single-gate sweep, in-place bit swap, basis init, logical-order gather,
+// probabilities, norm and scaling.  The fused chunk pass lives in sv_fused.cu.
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "sv_internal.h"
+#include "sv_arith.cuh"
+
+namespace svi {
+
+namespace {
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms = v > 0 ? v : 1;
+  }
+  return g_num_sms;
+}
+
+// Insert a zero bit at each of the `np` ascending positions pos[0..np).
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t i, const int8_t *pos, int np) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    if (j < np) {
+      const int p = pos[j];
+      i = ((i >> p) << (p + 1)) | (i & ((1ull << p) - 1));
+    }
+  }
+  return i;
+}
+
+struct SweepArgs {
+  DevGate g;
+  uint64_t nitems;   // pairs (or single amplitudes for GC_PHASE)
+  uint64_t setmask;  // OR'ed into the expanded index: control bits (and the target bit for GC_PHASE)
+  int8_t pos[8];     // ascending bit positions where a zero is inserted (target and controls)
+  int32_t npos;
+};
+
+constexpr int kSweepThreads = 256;
+constexpr int kSweepUnroll = 4;
+
+// One gate over the whole state (Algorithm 1, Sec. V.B): each item is a pair (k, k + 2^t) with bit t of k
+// zero and all control bits one.  Items are numbered by the remaining free bits, so consecutive threads
+// touch consecutive addresses whenever the target and controls are not among the lowest index bits.
+template <int MODE, int CLS>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(typename Arith<MODE>::G *__restrict__ psi, const SweepArgs a) {
+  using M = Arith<MODE>;
+  using G = typename M::G;
+  typename M::Coef c;
+  if (CLS != GC_X) M::coef(c, a.g);
+  const uint64_t tstride = 1ull << a.g.target;
+  const uint64_t tile = (uint64_t)kSweepThreads * kSweepUnroll;
+  for (uint64_t base = (uint64_t)blockIdx.x * tile; base < a.nitems; base += (uint64_t)gridDim.x * tile) {
+    uint64_t k0[kSweepUnroll];
+    G va[kSweepUnroll], vb[kSweepUnroll];
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; ++u) {
+      const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
+      k0[u] = insert_zeros(i, a.pos, a.npos) | a.setmask;
+      if (i < a.nitems) {
+        if (CLS == GC_PHASE) {
+          vb[u] = psi[k0[u]];
+        } else {
+          va[u] = psi[k0[u]];
+          vb[u] = psi[k0[u] + tstride];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; ++u) {
+      const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
+      if (i >= a.nitems) continue;
+      if (CLS == GC_X) {
+        psi[k0[u]] = vb[u];
+        psi[k0[u] + tstride] = va[u];
+      } else if (CLS == GC_PHASE) {
+        psi[k0[u]] = M::store(M::cmul(c, 3, M::load(vb[u])));
+      } else {
+        auto x = M::load(va[u]);
+        auto y = M::load(vb[u]);
+        apply_pair<MODE>(CLS, c, x, y);
+        psi[k0[u]] = M::store(x);
+        psi[k0[u] + tstride] = M::store(y);
+      }
+    }
+  }
+}
+
+template <int MODE, int CLS>
+cudaError_t sweep_launch(void *psi, const SweepArgs &a, cudaStream_t st) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep<MODE, CLS>, kSweepThreads, 0);
+    if (occ < 1) occ = 1;
+  }
+  const uint64_t tile = (uint64_t)kSweepThreads * kSweepUnroll;
+  const uint64_t need = (a.nitems + tile - 1) / tile;
+  const uint64_t cap = (uint64_t)num_sms() * occ;
+  const unsigned grid = (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
+  k_sweep<MODE, CLS><<<grid, kSweepThreads, 0, st>>>((typename Arith<MODE>::G *)psi, a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t sweep_mode(void *psi, const SweepArgs &a, cudaStream_t st) {
+  switch (a.g.cls) {
+    case GC_GENERAL: return sweep_launch<MODE, GC_GENERAL>(psi, a, st);
+    case GC_DIAG: return sweep_launch<MODE, GC_DIAG>(psi, a, st);
+    case GC_PHASE: return sweep_launch<MODE, GC_PHASE>(psi, a, st);
+    case GC_ANTIDIAG: return sweep_launch<MODE, GC_ANTIDIAG>(psi, a, st);
+    default: return sweep_launch<MODE, GC_X>(psi, a, st);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+template <typename G>
+__global__ void k_set_one(G *psi, uint64_t x) {
+  G v;
+  v.x = 1; v.y = 0;
+  psi[x] = v;
+}
+
+// In-place exchange of index bits a and b (a < b here): psi[..1_b..0_a..] <-> psi[..0_b..1_a..].  Pure moves.
+template <typename G>
+__global__ void __launch_bounds__(256) k_remap(G *__restrict__ psi, uint64_t nitems, int lo, int hi) {
+  const uint64_t ml = 1ull << lo, mh = 1ull << hi;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k = ((i >> lo) << (lo + 1)) | (i & (ml - 1));
+    k = ((k >> hi) << (hi + 1)) | (k & (mh - 1));
+    const G u = psi[k | ml], v = psi[k | mh];
+    psi[k | ml] = v;
+    psi[k | mh] = u;
+  }
+}
+
+struct Perm { int8_t p[kMaxQubits]; };
+
+__device__ __forceinline__ uint64_t logical_to_physical(uint64_t L, int n, const Perm &pm) {
+  uint64_t P = 0;
+  for (int t = 0; t < n; ++t) P |= ((L >> t) & 1ull) << pm.p[t];
+  return P;
+}
+
+template <typename G>
+__global__ void k_gather(const G *__restrict__ psi, int n, const Perm pm, uint64_t first, uint64_t count,
+                         const uint64_t *__restrict__ idx, G *__restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t L = idx ? idx[i] : first + i;
+    out[i] = psi[logical_to_physical(L, n, pm)];
+  }
+}
+
+// |alpha|^2 = re*re + im*im in double, each product and the sum rounded once (no contraction).
+template <typename G>
+__global__ void k_probs(const G *__restrict__ psi, int n, const Perm pm, uint64_t first, uint64_t count,
+                        double *__restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    const G v = psi[logical_to_physical(first + i, n, pm)];
+    const double re = (double)v.x, im = (double)v.y;
+    out[i] = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Norm: each thread accumulates |alpha|^2 of its amplitudes as a double-float (exact float products via
+// FMA, TwoSum accumulation), the block adds the per-thread values in FP64 in a fixed tree order, and a
+// second kernel adds the per-block partials in index order: the result does not depend on timing.
+// ------------------------------------------------------------------------------------------------------
+constexpr int kNormThreads = 256;
+constexpr int kNormBlocksPerSm = 4;
+
+__device__ __forceinline__ void acc_sq(float &s, float &c, float h, float l) {
+  const float p = __fmul_rn(h, h);
+  float e = __fmaf_rn(h, h, -p);
+  e = __fmaf_rn(2.0f * h, l, e);
+  float s2, err;
+  two_sum(s, p, s2, err);
+  s = s2;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+template <typename G, bool IS_DOUBLE>
+__global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ psi, uint64_t N, double *__restrict__ partials) {
+  float s = 0.f, c = 0.f;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    const G v = psi[i];
+    if (IS_DOUBLE) {
+      const dfv r = df_split((double)v.x), m = df_split((double)v.y);
+      acc_sq(s, c, r.h, r.l);
+      acc_sq(s, c, m.h, m.l);
+    } else {
+      acc_sq(s, c, (float)v.x, 0.f);
+      acc_sq(s, c, (float)v.y, 0.f);
+    }
+  }
+  __shared__ double red[kNormThreads];
+  red[threadIdx.x] = (double)s + (double)c;
+  __syncthreads();
+  for (int w = kNormThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_norm2(const double *__restrict__ partials, int nparts, double *__restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += partials[i];
+    out[0] = s;
+  }
+}
+
+template <typename G>
+__global__ void k_scale(G *__restrict__ psi, uint64_t N, const double *__restrict__ norm2) {
+  const double f = 1.0 / sqrt(norm2[0]);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    G v = psi[i];
+    v.x = (decltype(v.x))((double)v.x * f);
+    v.y = (decltype(v.y))((double)v.y * f);
+    psi[i] = v;
+  }
+}
+
+unsigned grid_for(uint64_t items, int threads) {
+  const uint64_t need = (items + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  return (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+Perm make_perm(const int *perm, int n) {
+  Perm p{};
+  for (int t = 0; t < n; ++t) p.p[t] = (int8_t)perm[t];
+  return p;
+}
+
+} // namespace
+
+// ------------------------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------------------------
+cudaError_t launch_sweep(void *psi, int n, int mode, const DevGate &g, cudaStream_t st) {
+  SweepArgs a{};
+  a.g = g;
+  int pos[8], np = 0;
+  pos[np++] = g.target;
+  uint64_t cm = g.cmask;
+  for (int b = 0; b < n; ++b)
+    if (cm >> b & 1ull) pos[np++] = b;
+  // ascending insertion sort (at most 5 entries)
+  for (int i = 1; i < np; ++i)
+    for (int j = i; j > 0 && pos[j - 1] > pos[j]; --j) { const int t = pos[j]; pos[j] = pos[j - 1]; pos[j - 1] = t; }
+  for (int i = 0; i < np; ++i) a.pos[i] = (int8_t)pos[i];
+  a.npos = np;
+  a.nitems = 1ull << (n - np);
+  a.setmask = cm | (g.cls == GC_PHASE ? (1ull << g.target) : 0ull);
+  switch (mode) {
+    case MODE_C64_F32: return sweep_mode<MODE_C64_F32>(psi, a, st);
+    case MODE_C128_F64: return sweep_mode<MODE_C128_F64>(psi, a, st);
+    default: return sweep_mode<MODE_C128_DF32>(psi, a, st);
+  }
+}
+
+cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream_t st) {
+  const size_t bytes = (mode == MODE_C64_F32 ? 8ull : 16ull) << n;
+  cudaError_t e = cudaMemsetAsync(psi, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  if (mode == MODE_C64_F32) k_set_one<float2><<<1, 1, 0, st>>>((float2 *)psi, x);
+  else k_set_one<double2><<<1, 1, 0, st>>>((double2 *)psi, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  const uint64_t items = 1ull << (n - 2);
+  const unsigned grid = grid_for(items, 256);
+  if (mode == MODE_C64_F32) k_remap<float2><<<grid, 256, 0, st>>>((float2 *)psi, items, lo, hi);
+  else k_remap<double2><<<grid, 256, 0, st>>>((double2 *)psi, items, lo, hi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void *psi, int n, int mode, const int *perm, uint64_t first, uint64_t count,
+                          const uint64_t *d_idx, void *d_out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const Perm pm = make_perm(perm, n);
+  const unsigned grid = grid_for(count, 256);
+  if (mode == MODE_C64_F32)
+    k_gather<float2><<<grid, 256, 0, st>>>((const float2 *)psi, n, pm, first, count, d_idx, (float2 *)d_out);
+  else
+    k_gather<double2><<<grid, 256, 0, st>>>((const double2 *)psi, n, pm, first, count, d_idx, (double2 *)d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probs(const void *psi, int n, int mode, const int *perm, uint64_t first, uint64_t count,
+                         double *d_out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const Perm pm = make_perm(perm, n);
+  const unsigned grid = grid_for(count, 256);
+  if (mode == MODE_C64_F32)
+    k_probs<float2><<<grid, 256, 0, st>>>((const float2 *)psi, n, pm, first, count, d_out);
+  else
+    k_probs<double2><<<grid, 256, 0, st>>>((const double2 *)psi, n, pm, first, count, d_out);
+  return cudaGetLastError();
+}
+
+int norm_parts() { return num_sms() * kNormBlocksPerSm; }
+
+cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st) {
+  const int parts = norm_parts();
+  const uint64_t N = 1ull << n;
+  if (mode == MODE_C64_F32)
+    k_norm1<float2, false><<<parts, kNormThreads, 0, st>>>((const float2 *)psi, N, d_partials);
+  else
+    k_norm1<double2, true><<<parts, kNormThreads, 0, st>>>((const double2 *)psi, N, d_partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_norm2<<<1, 32, 0, st>>>(d_partials, parts, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cudaStream_t st) {
+  const uint64_t N = 1ull << n;
+  const unsigned grid = grid_for(N, 256);
+  if (mode == MODE_C64_F32) k_scale<float2><<<grid, 256, 0, st>>>((float2 *)psi, N, d_norm2);
+  else k_scale<double2><<<grid, 256, 0, st>>>((double2 *)psi, N, d_norm2);
+  return cudaGetLastError();
+}
+
+} // namespace svi

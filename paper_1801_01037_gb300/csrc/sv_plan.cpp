@@ -1,0 +1,321 @@
+// Host planner.  See sv_plan.h.
+#include "sv_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <set>
+
+namespace svi {
+
+static bool eq(double a, double b) { return a == b; }
+
+int classify(const double *U) {
+  const bool q11_zero = eq(U[0], 0) && eq(U[1], 0), q12_zero = eq(U[2], 0) && eq(U[3], 0);
+  const bool q21_zero = eq(U[4], 0) && eq(U[5], 0), q22_zero = eq(U[6], 0) && eq(U[7], 0);
+  const bool q11_one = eq(U[0], 1) && eq(U[1], 0), q22_one = eq(U[6], 1) && eq(U[7], 0);
+  if (q12_zero && q21_zero) {
+    if (q11_one && q22_one) return -1;
+    return q11_one ? GC_PHASE : GC_DIAG;
+  }
+  if (q11_zero && q22_zero) {
+    const bool q12_one = eq(U[2], 1) && eq(U[3], 0), q21_one = eq(U[4], 1) && eq(U[5], 0);
+    return (q12_one && q21_one) ? GC_X : GC_ANTIDIAG;
+  }
+  return GC_GENERAL;
+}
+
+void fill_coefficients(DevGate &g, const double *U) {
+  for (int i = 0; i < 8; ++i) {
+    g.q[i] = U[i];
+    g.qf[i] = (float)U[i];
+    g.qh[i] = (float)U[i];
+    g.ql[i] = (float)(U[i] - (double)g.qh[i]);
+  }
+}
+
+int validate_gate(const sv_gate &g, int n, std::string &why) {
+  char buf[160];
+  if (g.kind == SV_GATE_SWAP) {
+    if (g.target < 0 || g.target >= n || g.target2 < 0 || g.target2 >= n || g.target == g.target2) {
+      snprintf(buf, sizeof buf, "SWAP qubits (%d, %d) must be distinct and in [0, %d)", g.target, g.target2, n);
+      why = buf;
+      return SV_ERR_ARG;
+    }
+    if (g.ncontrols != 0) {
+      why = "controlled SWAP is not supported";
+      return SV_ERR_ARG;
+    }
+    return SV_OK;
+  }
+  if (g.kind != SV_GATE_U) {
+    snprintf(buf, sizeof buf, "unknown gate kind %d", g.kind);
+    why = buf;
+    return SV_ERR_ARG;
+  }
+  if (g.target < 0 || g.target >= n) {
+    snprintf(buf, sizeof buf, "target %d out of range [0, %d)", g.target, n);
+    why = buf;
+    return SV_ERR_ARG;
+  }
+  if (g.ncontrols < 0 || g.ncontrols > SV_MAX_CONTROLS) {
+    snprintf(buf, sizeof buf, "ncontrols %d out of range [0, %d]", g.ncontrols, SV_MAX_CONTROLS);
+    why = buf;
+    return SV_ERR_ARG;
+  }
+  uint64_t seen = 1ull << g.target;
+  for (int i = 0; i < g.ncontrols; ++i) {
+    const int c = g.controls[i];
+    if (c < 0 || c >= n || (seen >> c & 1ull)) {
+      snprintf(buf, sizeof buf, "control %d is out of range, equal to the target or repeated", c);
+      why = buf;
+      return SV_ERR_ARG;
+    }
+    seen |= 1ull << c;
+  }
+  // U^dagger U = I within 1e-10 (entries finite).
+  const double *u = g.U;
+  for (int i = 0; i < 8; ++i)
+    if (!std::isfinite(u[i])) {
+      why = "gate matrix has a non-finite entry";
+      return SV_ERR_NOT_UNITARY;
+    }
+  double worst = 0;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      // (U^dagger U)_ij = sum_r conj(U_ri) U_rj
+      double re = 0, im = 0;
+      for (int r = 0; r < 2; ++r) {
+        const double ar = u[4 * r + 2 * i], ai = -u[4 * r + 2 * i + 1];
+        const double br = u[4 * r + 2 * j], bi = u[4 * r + 2 * j + 1];
+        re += ar * br - ai * bi;
+        im += ar * bi + ai * br;
+      }
+      worst = std::max(worst, std::fabs(re - (i == j ? 1.0 : 0.0)));
+      worst = std::max(worst, std::fabs(im));
+    }
+  if (worst > 1e-10) {
+    snprintf(buf, sizeof buf, "gate matrix is not unitary (max |U^dagger U - I| = %.3g)", worst);
+    why = buf;
+    return SV_ERR_NOT_UNITARY;
+  }
+  return SV_OK;
+}
+
+std::vector<std::pair<int, int>> canonicalize_steps(std::vector<int> &perm) {
+  std::vector<std::pair<int, int>> out;
+  const int n = (int)perm.size();
+  for (int t = 0; t < n; ++t) {
+    if (perm[t] == t) continue;
+    int u = 0;
+    while (perm[u] != t) ++u;
+    out.emplace_back(perm[t], t);  // exchange physical bits perm[t] and t
+    perm[u] = perm[t];
+    perm[t] = t;
+  }
+  return out;
+}
+
+namespace {
+
+struct Sched {
+  int idx;        // source gate index
+  int cls;
+  int pt;         // physical target
+  uint64_t pc;    // physical control mask
+};
+
+DevGate to_sweep_gate(const sv_gate &g, const Sched &s) {
+  DevGate d;
+  std::memset(&d, 0, sizeof d);
+  fill_coefficients(d, g.U);
+  d.cls = (uint32_t)s.cls;
+  d.target = s.pt;
+  d.cmask = s.pc;
+  return d;
+}
+
+} // namespace
+
+void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &P) {
+  P = Plan();
+  P.gate_step.assign(ngates, -1);
+  P.gate_order.assign(ngates, -1);
+  int order = 0;
+  const int k = std::min(cfg.k, n);
+  int c = std::min(cfg.c, k);
+  c = std::max(c, std::min(3, k));
+
+  auto sched_of = [&](size_t i, int cls) {
+    Sched s;
+    s.idx = (int)i;
+    s.cls = cls;
+    s.pt = perm[gates[i].target];
+    s.pc = 0;
+    for (int j = 0; j < gates[i].ncontrols; ++j) s.pc |= 1ull << perm[gates[i].controls[j]];
+    return s;
+  };
+
+  if (!cfg.fusion) {
+    for (size_t i = 0; i < ngates; ++i) {
+      const sv_gate &g = gates[i];
+      P.gate_order[i] = order++;
+      if (g.kind == SV_GATE_SWAP) {
+        std::swap(perm[g.target], perm[g.target2]);
+        ++P.n_relabels;
+        continue;
+      }
+      const int cls = classify(g.U);
+      if (cls < 0) { ++P.n_skipped; continue; }
+      const Sched s = sched_of(i, cls);
+      P.sweep_gates.push_back(to_sweep_gate(g, s));
+      P.gate_step[i] = (int)P.steps.size();
+      P.step_qmask.push_back(1ull << s.pt);
+      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+      ++P.n_sweep_gates;
+    }
+    return;
+  }
+
+  // Per-qubit queues of the gates touching each qubit; a gate is ready when it heads all of its queues.
+  std::vector<std::vector<int>> q(n);
+  std::vector<int> cls_of(ngates);
+  auto qubits_of = [&](size_t i, int *out) {
+    int m = 0;
+    const sv_gate &g = gates[i];
+    out[m++] = g.target;
+    if (g.kind == SV_GATE_SWAP) out[m++] = g.target2;
+    else
+      for (int j = 0; j < g.ncontrols; ++j) out[m++] = g.controls[j];
+    return m;
+  };
+  for (size_t i = 0; i < ngates; ++i) {
+    int qs[6];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j) q[qs[j]].push_back((int)i);
+    cls_of[i] = gates[i].kind == SV_GATE_SWAP ? -2 : classify(gates[i].U);
+  }
+  std::vector<size_t> head(n, 0);
+  auto is_ready = [&](int i) {
+    int qs[6];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j)
+      if (head[qs[j]] >= q[qs[j]].size() || q[qs[j]][head[qs[j]]] != i) return false;
+    return true;
+  };
+  std::set<int> ready;
+  for (int u = 0; u < n; ++u)
+    if (!q[u].empty() && is_ready(q[u][0])) ready.insert(q[u][0]);
+  auto pop = [&](int i) {
+    ready.erase(i);
+    int qs[6];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j) ++head[qs[j]];
+    for (int j = 0; j < m; ++j) {
+      const int u = qs[j];
+      if (head[u] < q[u].size() && is_ready(q[u][head[u]])) ready.insert(q[u][head[u]]);
+    }
+  };
+  auto needs_pairing = [](int cls) { return cls == GC_GENERAL || cls == GC_ANTIDIAG || cls == GC_X; };
+
+  bool first_pass = true;
+  while (!ready.empty() || (first_pass && cfg.init_first)) {
+    bool inQ[64] = {false};
+    int qcount = 0;
+    if (k == n) {
+      for (int b = 0; b < n; ++b) inQ[b] = true;
+      qcount = n;
+    } else {
+      for (int b = 0; b < c; ++b) inQ[b] = true;
+      qcount = c;
+    }
+    std::vector<Sched> pg;
+    for (;;) {
+      int chosen = -1;
+      for (int i : ready) {
+        const int cls = cls_of[i];
+        if (cls == -2 || cls == -1) { chosen = i; break; }
+        if (!needs_pairing(cls) || inQ[perm[gates[i].target]]) { chosen = i; break; }
+      }
+      if (chosen >= 0) {
+        const int cls = cls_of[chosen];
+        P.gate_order[chosen] = order++;
+        if (cls == -2) {
+          std::swap(perm[gates[chosen].target], perm[gates[chosen].target2]);
+          ++P.n_relabels;
+        } else if (cls == -1) {
+          ++P.n_skipped;
+        } else {
+          pg.push_back(sched_of(chosen, cls));
+        }
+        pop(chosen);
+        continue;
+      }
+      if (qcount >= k || ready.empty()) break;
+      // Add the physical bit that the most ready gates are waiting for (ties: the earliest gate).
+      int best_bit = -1, best_count = 0;
+      int counts[64] = {0};
+      for (int i : ready) {
+        const int b = perm[gates[i].target];
+        if (++counts[b] > best_count) { best_count = counts[b]; best_bit = b; }
+      }
+      if (best_bit < 0) break;
+      inQ[best_bit] = true;
+      ++qcount;
+    }
+    const bool init_here = first_pass && cfg.init_first;
+    first_pass = false;
+    if (pg.empty() && !init_here) continue;
+    if (pg.size() == 1 && cfg.single_as_sweep && !init_here) {
+      P.gate_step[pg[0].idx] = (int)P.steps.size();
+      P.step_qmask.push_back(1ull << pg[0].pt);
+      P.sweep_gates.push_back(to_sweep_gate(gates[pg[0].idx], pg[0]));
+      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+      ++P.n_sweep_gates;
+      continue;
+    }
+    // Fill Q up to k bits with the lowest unused bits, so every pass has chunks of exactly 2^k amplitudes.
+    for (int b = 0; b < n && qcount < k; ++b)
+      if (!inQ[b]) { inQ[b] = true; ++qcount; }
+    PassDesc d;
+    std::memset(&d, 0, sizeof d);
+    d.n = n;
+    d.k = k;
+    d.c = c;
+    int local[64];
+    int j = 0;
+    for (int b = 0; b < n; ++b)
+      if (inQ[b]) {
+        local[b] = j;
+        d.qpos[j] = (int8_t)b;
+        d.qpos_out[j] = (int8_t)b;
+        d.qmask |= 1ull << b;
+        ++j;
+      }
+    d.init = init_here ? 1 : 0;
+    d.init_x = cfg.init_x;
+    d.ngates = (int)pg.size();
+    P.pass_gate_offset.push_back((int)P.fused_gates.size());
+    for (const Sched &s : pg) {
+      DevGate g;
+      std::memset(&g, 0, sizeof g);
+      fill_coefficients(g, gates[s.idx].U);
+      g.cls = (uint32_t)s.cls;
+      if (inQ[s.pt]) g.target = local[s.pt];
+      else { g.target = -1; g.tmask = 1ull << s.pt; }
+      for (int b = 0; b < n; ++b)
+        if (s.pc >> b & 1ull) {
+          if (inQ[b]) g.cmask |= 1ull << local[b];
+          else g.gmask |= 1ull << b;
+        }
+      P.fused_gates.push_back(g);
+    }
+    for (const Sched &s : pg) P.gate_step[s.idx] = (int)P.steps.size();
+    P.step_qmask.push_back(d.qmask);
+    P.passes.push_back(d);
+    P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, (int)pg.size()});
+    P.n_fused_gates += (int)pg.size();
+  }
+}
+
+} // namespace svi

@@ -1,0 +1,57 @@
+// Host planner: gate classification, layout map (logical -> physical qubit) and fusion of gates into
+// chunk passes.  Pure host code; it launches nothing.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "sv_internal.h"
+#include "../../include/sv.h"
+
+namespace svi {
+
+struct PlanConfig {
+  int k = 12;               // chunk qubits (2^k amplitudes per chunk)
+  int c = 4;                // contiguous low bits always in a chunk
+  bool fusion = true;       // false: every gate becomes a single-gate sweep
+  bool single_as_sweep = true;  // a pass holding one gate is emitted as a sweep instead
+  bool init_first = false;  // the first pass starts from |init_x> (batched / served states)
+  uint64_t init_x = 0;
+};
+
+struct Step {
+  enum Kind { FUSED = 0, SWEEP = 1, REMAP = 2 } kind;
+  int index;   // FUSED: pass index; SWEEP: sweep gate index
+  int a, b;    // REMAP: physical bits to exchange
+  int ngates;  // source gates this step applies
+};
+
+struct Plan {
+  std::vector<Step> steps;
+  std::vector<PassDesc> passes;      // psi / gates pointers are filled in at launch
+  std::vector<int> pass_gate_offset; // first DevGate of each pass in fused_gates
+  std::vector<DevGate> fused_gates;
+  std::vector<DevGate> sweep_gates;
+  int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_remaps = 0, n_skipped = 0;
+  // Schedule record per source gate: the step that applies it (-1: folded into the layout or skipped) and
+  // its position in execution order; per step the physical bits its chunks span (a sweep: its target bit).
+  std::vector<int> gate_step, gate_order;
+  std::vector<uint64_t> step_qmask;
+};
+
+// Classify U (8 doubles) by exact comparisons; returns -1 for the identity.
+int classify(const double *U);
+
+// Fill q / qf / qh / ql of a DevGate from U.
+void fill_coefficients(DevGate &g, const double *U);
+
+// Validate one record against n qubits: qubits in range and distinct, U unitary within 1e-10.
+// Returns SV_OK or an sv_status error with `why` set.
+int validate_gate(const sv_gate &g, int n, std::string &why);
+
+// Plan `ngates` validated records; perm (logical -> physical) is read and updated by SWAP relabelling.
+void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &out);
+
+// Transpositions (physical bit pairs) that bring `perm` back to the identity, in order; updates perm.
+std::vector<std::pair<int, int>> canonicalize_steps(std::vector<int> &perm);
+
+} // namespace svi

@@ -1,0 +1,268 @@
+// C ABI: read-out in logical order, checkpoint write, norm, renormalisation and the CUDA-graph apply path.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "sv_state.h"
+
+using namespace svi;
+
+namespace {
+
+constexpr uint64_t kReadChunk = 1ull << 22;  // amplitudes per gather round trip
+
+bool identity_layout(const sv_state *s) {
+  for (int t = 0; t < s->n; ++t)
+    if (s->perm[t] != t) return false;
+  return true;
+}
+
+int ensure_read_buffer(sv_state *s, size_t bytes) {
+  if (bytes <= s->d_read_cap) return SV_OK;
+  cudaError_t e;
+  if (s->d_read) {
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "stream sync");
+    cudaFree(s->d_read);
+    s->d_read = nullptr;
+    s->d_read_cap = 0;
+  }
+  if ((e = cudaMalloc(&s->d_read, bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SV_ERR_OOM, "read-out staging allocation failed");
+  }
+  s->d_read_cap = bytes;
+  return SV_OK;
+}
+
+int check_range(const sv_state *s, uint64_t first, uint64_t count) {
+  const uint64_t dim = 1ull << s->n;
+  if (first > dim || count > dim - first) return set_error(SV_ERR_ARG, "index range exceeds 2^n");
+  return SV_OK;
+}
+
+void free_entry(GraphEntry &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.d_gates) cudaFree(g.d_gates);
+  for (cudaEvent_t ev : g.evs) cudaEventDestroy(ev);
+  g.exec = nullptr;
+  g.d_gates = nullptr;
+  g.evs.clear();
+}
+
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h) {
+  const unsigned char *b = (const unsigned char *)p;
+  for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+} // namespace
+
+extern "C" {
+
+sv_status sv_read_amplitudes(sv_state *s, uint64_t first, uint64_t count, void *host_out) {
+  if (!s || (!host_out && count)) return set_error(SV_ERR_ARG, "NULL argument");
+  int rc = check_range(s, first, count);
+  if (rc != SV_OK) return rc;
+  if (count == 0) return SV_OK;
+  const size_t ab = amp_bytes(s->dtype);
+  cudaError_t e;
+  if (identity_layout(s)) {
+    e = cudaMemcpyAsync(host_out, (const char *)s->psi + first * ab, count * ab, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? SV_OK : cuda_fail(e, "read amplitudes");
+  }
+  const uint64_t chunk = std::min<uint64_t>(count, kReadChunk);
+  if ((rc = ensure_read_buffer(s, chunk * ab)) != SV_OK) return rc;
+  for (uint64_t off = 0; off < count; off += chunk) {
+    const uint64_t m = std::min(chunk, count - off);
+    e = launch_gather(s->psi, s->n, mode_of(s), s->perm.data(), first + off, m, nullptr, s->d_read, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char *)host_out + off * ab, s->d_read, m * ab, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gather amplitudes");
+  }
+  return SV_OK;
+}
+
+sv_status sv_read_amplitudes_at(sv_state *s, const uint64_t *idx, uint64_t count, void *host_out) {
+  if (!s || ((!idx || !host_out) && count)) return set_error(SV_ERR_ARG, "NULL argument");
+  const uint64_t dim = 1ull << s->n;
+  for (uint64_t i = 0; i < count; ++i)
+    if (idx[i] >= dim) return set_error(SV_ERR_ARG, "index " + std::to_string(i) + " out of range");
+  if (count == 0) return SV_OK;
+  const size_t ab = amp_bytes(s->dtype);
+  const uint64_t chunk = std::min<uint64_t>(count, kReadChunk);
+  int rc = ensure_read_buffer(s, chunk * (ab + sizeof(uint64_t)));
+  if (rc != SV_OK) return rc;
+  uint64_t *d_idx = (uint64_t *)((char *)s->d_read + chunk * ab);
+  for (uint64_t off = 0; off < count; off += chunk) {
+    const uint64_t m = std::min(chunk, count - off);
+    cudaError_t e = cudaMemcpyAsync(d_idx, idx + off, m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = launch_gather(s->psi, s->n, mode_of(s), s->perm.data(), 0, m, d_idx, s->d_read, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char *)host_out + off * ab, s->d_read, m * ab, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gather amplitudes");
+  }
+  return SV_OK;
+}
+
+sv_status sv_read_probabilities(sv_state *s, uint64_t first, uint64_t count, double *host_out) {
+  if (!s || (!host_out && count)) return set_error(SV_ERR_ARG, "NULL argument");
+  int rc = check_range(s, first, count);
+  if (rc != SV_OK) return rc;
+  if (count == 0) return SV_OK;
+  const uint64_t chunk = std::min<uint64_t>(count, kReadChunk);
+  if ((rc = ensure_read_buffer(s, chunk * sizeof(double))) != SV_OK) return rc;
+  for (uint64_t off = 0; off < count; off += chunk) {
+    const uint64_t m = std::min(chunk, count - off);
+    cudaError_t e = launch_probs(s->psi, s->n, mode_of(s), s->perm.data(), first + off, m, (double *)s->d_read, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host_out + off, s->d_read, m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "probabilities");
+  }
+  return SV_OK;
+}
+
+sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const void *host_in) {
+  if (!s || (!host_in && count)) return set_error(SV_ERR_ARG, "NULL argument");
+  int rc = check_range(s, first, count);
+  if (rc != SV_OK) return rc;
+  if (!identity_layout(s) && (rc = canonicalize_now(s)) != SV_OK) return rc;
+  const size_t ab = amp_bytes(s->dtype);
+  cudaError_t e = cudaMemcpyAsync((char *)s->psi + first * ab, host_in, count * ab, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "write amplitudes");
+}
+
+sv_status sv_norm(sv_state *s, double *out) {
+  if (!s || !out) return set_error(SV_ERR_ARG, "NULL argument");
+  double *d_out = s->d_scalars + norm_parts();
+  cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "norm");
+}
+
+sv_status sv_renormalize(sv_state *s) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  double *d_out = s->d_scalars + norm_parts();
+  cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
+  if (e == cudaSuccess) e = launch_scale(s->psi, s->n, mode_of(s), d_out, s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "renormalise");
+}
+
+// Capture the planned launches once per (gates, layout, state, options) and replay the graph afterwards.
+sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngates) {
+  if (!s || (!gates && ngates)) return set_error(SV_ERR_ARG, "NULL argument");
+  for (size_t i = 0; i < ngates; ++i) {
+    std::string why;
+    const int rc = validate_gate(gates[i], s->n, why);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+  }
+  const PlanConfig cfg = plan_config(s);
+  uint64_t key = 1469598103934665603ull;
+  key = hash_bytes(gates, ngates * sizeof(sv_gate), key);
+  key = hash_bytes(s->perm.data(), s->perm.size() * sizeof(int), key);
+  const int opts[6] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical};
+  key = hash_bytes(opts, sizeof opts, key);
+  key = hash_bytes(&s->psi, sizeof s->psi, key);
+  auto it = s->graphs.find(key);
+  cudaError_t e;
+  if (it != s->graphs.end() && it->second.perm_before == s->perm && (it->second.evs.empty() != (s->profile != 0))) {
+    if ((e = cudaGraphLaunch(it->second.exec, s->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    s->perm = it->second.perm_after;
+    s->last_evs = it->second.evs.empty() ? nullptr : it->second.evs.data();
+    s->last_kind = it->second.ev_kind;
+    return SV_OK;
+  }
+  if (it != s->graphs.end()) {  // same key captured with the other profiling setting: replace it
+    cudaStreamSynchronize(s->stream);
+    free_entry(it->second);
+    s->graphs.erase(it);
+  }
+  if (s->graphs.size() >= 64) {
+    cudaStreamSynchronize(s->stream);
+    for (auto &kv : s->graphs) free_entry(kv.second);
+    s->graphs.clear();
+  }
+  GraphEntry ent;
+  ent.perm_before = s->perm;
+  std::vector<int> perm = s->perm;
+  Plan P;
+  make_plan(s->n, cfg, perm, gates, ngates, P);
+  if (!P.fused_gates.empty()) {
+    if ((e = cudaMalloc(&ent.d_gates, P.fused_gates.size() * sizeof(DevGate))) != cudaSuccess)
+      return set_error(SV_ERR_OOM, "graph gate buffer allocation failed");
+    if ((e = cudaMemcpy(ent.d_gates, P.fused_gates.data(), P.fused_gates.size() * sizeof(DevGate),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+      cudaFree(ent.d_gates);
+      return cuda_fail(e, "graph gate upload");
+    }
+  }
+  if (s->profile) {
+    for (size_t i = 0; i < 2 * P.steps.size(); ++i) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+        for (cudaEvent_t x : ent.evs) cudaEventDestroy(x);
+        cudaFree(ent.d_gates);
+        return cuda_fail(e, "profiling event");
+      }
+      ent.evs.push_back(ev);
+    }
+    ent.ev_kind = step_kinds(P);
+  }
+  cudaStream_t cap = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    free_entry(ent);
+    return cuda_fail(e, "capture stream");
+  }
+  // Renormalisation is not part of a captured graph.
+  const int64_t saved_period = s->renorm_period;
+  s->renorm_period = 0;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  int rc = SV_OK;
+  if (e == cudaSuccess) {
+    rc = run_plan(s, P, ent.d_gates, nullptr, cap, ent.evs.empty() ? nullptr : ent.evs.data(), true);
+    if (rc == SV_OK && s->canonical) {
+      std::vector<int> pp = perm;
+      for (const auto &ab : canonicalize_steps(pp)) {
+        const cudaError_t e2 = launch_remap_swap(s->psi, s->n, mode_of(s), ab.first, ab.second, cap);
+        if (e2 != cudaSuccess) { rc = cuda_fail(e2, "bit-swap pass"); break; }
+      }
+      perm = pp;
+    }
+    e = cudaStreamEndCapture(cap, &graph);
+  }
+  s->renorm_period = saved_period;
+  cudaStreamDestroy(cap);
+  if (rc != SV_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    free_entry(ent);
+    return rc != SV_OK ? rc : cuda_fail(e, "stream capture");
+  }
+  e = cudaGraphInstantiate(&ent.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    free_entry(ent);
+    return cuda_fail(e, "graph instantiate");
+  }
+  ent.perm_after = perm;
+  if ((e = cudaGraphLaunch(ent.exec, s->stream)) != cudaSuccess) {
+    free_entry(ent);
+    return cuda_fail(e, "graph launch");
+  }
+  s->perm = perm;
+  s->st_passes = (int)P.passes.size();
+  s->st_fused = P.n_fused_gates;
+  s->st_sweeps = P.n_sweep_gates;
+  s->st_relabels = P.n_relabels;
+  auto ins = s->graphs.emplace(key, std::move(ent));
+  s->last_evs = ins.first->second.evs.empty() ? nullptr : ins.first->second.evs.data();
+  s->last_kind = ins.first->second.ev_kind;
+  return SV_OK;
+}
+
+} // extern "C"

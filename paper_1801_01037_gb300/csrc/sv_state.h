@@ -1,0 +1,78 @@
+// Host-side state handle and helpers shared by the API, the batch runner and the server.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+#include <cuda_runtime.h>
+#include "sv_internal.h"
+#include "sv_plan.h"
+#include "../../include/sv.h"
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  svi::DevGate *d_gates = nullptr;
+  std::vector<cudaEvent_t> evs;   // profiling: two events per launch, recorded by the graph itself
+  std::vector<int> ev_kind;
+  std::vector<int> perm_before, perm_after;
+  size_t nbytes = 0;
+};
+
+struct sv_state {
+  int n = 0;
+  sv_dtype dtype = SV_C128;
+  int arith = SV_ARITH_AUTO;
+  void *psi = nullptr;
+  bool owned = true;
+  cudaStream_t stream = nullptr;
+  std::vector<int> perm;      // logical qubit -> physical bit
+  int chunk_k = 0;            // 0 = default
+  int fusion = 1;
+  int canonical = 0;
+  int64_t renorm_period = 0;
+  int64_t gates_since_renorm = 0;
+  // device gate buffer and its pinned staging copy
+  svi::DevGate *d_gates = nullptr;
+  size_t d_gates_cap = 0;
+  svi::DevGate *h_stage = nullptr;
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  bool stage_pending = false;
+  // norm scratch: norm_parts() partials + 1 result
+  double *d_scalars = nullptr;
+  // read-out staging (device)
+  void *d_read = nullptr;
+  size_t d_read_cap = 0;
+  // stats of the last apply
+  int st_passes = 0, st_fused = 0, st_sweeps = 0, st_relabels = 0, st_remaps = 0;
+  std::unordered_map<uint64_t, GraphEntry> graphs;
+  // profiling (SV_OPT_PROFILE)
+  int profile = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  const cudaEvent_t *last_evs = nullptr;
+  std::vector<int> last_kind;
+};
+
+namespace svi {
+
+int set_error(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+int mode_of(const sv_state *s);
+size_t amp_bytes(sv_dtype dt);
+int check_device();
+PlanConfig plan_config(const sv_state *s);
+// Upload DevGates through the state's pinned staging buffer into its device gate buffer.
+int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<DevGate> &b, DevGate **d_a,
+                 DevGate **d_b);
+// Launch the steps of a plan (gates already on the device at d_fused / d_sweep) on stream st.
+// evs: nullptr, or two timing events per step recorded around each launch (external records when capturing).
+int run_plan(sv_state *s, const Plan &P, DevGate *d_fused, DevGate *d_sweep, cudaStream_t st,
+             const cudaEvent_t *evs = nullptr, bool capturing = false);
+// Make sure the state's event pool holds at least 2 * steps events.
+int ensure_event_pool(sv_state *s, size_t steps);
+std::vector<int> step_kinds(const Plan &P);
+int canonicalize_now(sv_state *s);
+int maybe_renormalize(sv_state *s, int applied);
+int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero);
+
+} // namespace svi

@@ -1,0 +1,152 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point declared in include/sv.h,
+rejects bad arguments on the host before any device work, and its planner (host logic) produces schedules
+that are valid reorderings of the circuit.  The planner check replays the planned execution order through
+the FP64 oracle and compares with the original order."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import circuits as C
+import oracle
+from conftest import ROOT
+
+pkg = pytest.importorskip("paper_1801_01037_gb300")
+B = pkg._binding
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_01037_gb300 import build
+    build.build()
+    return B.load()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:sv_status|const char \*)\s*(sv_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 25
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(B.EXPORTED) == names
+
+
+def test_gate_record_matches_header(lib):
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    assert "double U[8];" in src and C.GATE_DTYPE.itemsize == 96
+
+
+def test_null_and_range_errors_without_device(lib):
+    import ctypes
+    assert lib.sv_destroy(None) == B.SV_OK
+    assert lib.sv_apply_gate(None, None, 0, None, 0) == B.SV_ERR_ARG
+    out = ctypes.c_void_p()
+    assert lib.sv_create(0, B.SV_C128, None, ctypes.byref(out)) == B.SV_ERR_ARG
+    assert lib.sv_create(37, B.SV_C128, None, ctypes.byref(out)) == B.SV_ERR_ARG
+    assert lib.sv_create(4, 7, None, ctypes.byref(out)) == B.SV_ERR_ARG
+    assert lib.sv_norm(None, None) == B.SV_ERR_ARG
+    assert lib.sv_poll(None, 1, None, None) == B.SV_ERR_ARG
+    assert b"NULL" in lib.sv_last_error()
+
+
+def test_no_device_is_reported_not_hidden(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.sv_create(4, B.SV_C128, None, ctypes.byref(out)) == B.SV_ERR_NO_DEVICE
+
+
+def test_validation_rejects_bad_gates(lib):
+    bad = [
+        C.pack([C.gate_u(C.X, 5)]),                   # target out of range
+        C.pack([C.gate_u(C.X, 1, (1,))]),             # control == target
+        C.pack([C.gate_u(C.X, 1, (0, 0))]),           # repeated control
+        C.pack([C.gate_swap(2, 2)]),                  # SWAP of one qubit
+    ]
+    for g in bad:
+        with pytest.raises(B.SvError) as e:
+            B.sv_plan_dry_run(4, B.SV_C128, g)
+        assert e.value.code == B.SV_ERR_ARG
+    nonunitary = C.pack([C.gate_u(np.array([[1, 0], [0, 1.001]]), 0)])
+    with pytest.raises(B.SvError) as e:
+        B.sv_plan_dry_run(4, B.SV_C128, nonunitary)
+    assert e.value.code == B.SV_ERR_NOT_UNITARY
+
+
+def replay_in_plan_order(n, gates, plan):
+    """The circuit's gates in the planner's execution order."""
+    order = plan["order_of_gate"]
+    assert sorted(order) == list(range(len(gates)))
+    return gates[np.argsort(order)]
+
+
+PLAN_CASES = [
+    ("random", lambda: C.random_workload(14, 6, seed=5).gates, 14),
+    ("qft", lambda: C.pack(C.qft(13)), 13),
+    ("qft_random", lambda: C.qft_random_workload(15, 3, seed=8).gates, 15),
+    ("mixed", lambda: C.pack(C.ghz(12) + [C.gate_swap(0, 11), C.gate_u(C.haar_u2(np.random.default_rng(1)), 11, (0, 3, 7))]
+                             + C.random_layers(12, 2, np.random.default_rng(2))), 12),
+]
+
+
+@pytest.mark.parametrize("name,make,n", PLAN_CASES, ids=[c[0] for c in PLAN_CASES])
+@pytest.mark.parametrize("dtype,chunk_k", [(B.SV_C128, 0), (B.SV_C64, 0), (B.SV_C128, 8)])
+def test_planner_schedule_is_a_valid_reordering(lib, name, make, n, dtype, chunk_k):
+    gates = make()
+    plan = B.sv_plan_dry_run(n, dtype, gates, chunk_k)
+    # 1. gates sharing a qubit keep their relative order
+    order = plan["order_of_gate"]
+    last = {}
+    for i, g in enumerate(gates):
+        qs = [int(g["target"])] + ([int(g["target2"])] if g["kind"] == C.GATE_SWAP else
+                                   [int(c) for c in g["controls"][:g["ncontrols"]]])
+        for q in qs:
+            if q in last:
+                assert order[i] > order[last[q]]
+            last[q] = i
+    # 2. the reordered circuit gives the same state (FP64 oracle)
+    want = oracle.simulate(n, gates, 3)
+    got = oracle.simulate(n, replay_in_plan_order(n, gates, plan), 3)
+    assert np.max(np.abs(got - want)) < 1e-12
+    # 3. launches apply gates in order, and every pairing gate's physical target lies in its launch's chunk bits
+    steps = plan["step_of_gate"]
+    perm = list(range(n))
+    for i in np.argsort(order):
+        g = gates[i]
+        if g["kind"] == C.GATE_SWAP:
+            a, b = int(g["target"]), int(g["target2"])
+            perm[a], perm[b] = perm[b], perm[a]
+            assert steps[i] == -1
+            continue
+        u = C.unpack_u(g)
+        if np.array_equal(u, np.eye(2)):
+            assert steps[i] == -1
+            continue
+        assert steps[i] >= 0
+        diagonal = u[0, 1] == 0 and u[1, 0] == 0
+        if not diagonal:
+            assert plan["step_qmask"][steps[i]] >> np.uint64(perm[int(g["target"])]) & np.uint64(1)
+    assert list(plan["final_perm"]) == perm
+    # steps are visited in non-decreasing order along the execution order
+    seq = [steps[i] for i in np.argsort(order) if steps[i] >= 0]
+    assert seq == sorted(seq)
+
+
+def test_fusion_reduces_launches(lib):
+    w = C.random_workload(30, 20, seed=1002)
+    plan = B.sv_plan_dry_run(30, B.SV_C128, w.gates)
+    assert plan["nsteps"] < len(w.gates) // 5
+
+
+def test_swaps_fold_into_layout(lib):
+    """The QFT's closing SWAPs never become launches: they relabel qubits (Sec. VI.B)."""
+    n = 10
+    plan = B.sv_plan_dry_run(n, B.SV_C128, C.pack(C.qft(n)))
+    assert list(plan["final_perm"]) == list(range(n))[::-1]

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element, on seeded inputs.
+
+Sizes run from n = 1 (one pair) through n = 18 (64 chunks of 2^12), so the fused pass is exercised with a
+single chunk, with exactly one chunk, with many chunks, and the single-gate sweep with ragged tails (fewer
+items than one tile).  Tolerances are in ``gpu_helpers``."""
+import numpy as np
+import pytest
+
+import circuits as C
+import oracle
+from gpu_helpers import MODES, MODE_IDS, assert_close, make_state, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_1801_01037_gb300")._binding
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1801_01037_gb300 import build
+    build.build()
+    B.load()
+
+
+def class_matrices(rng):
+    u = C.haar_u2(rng)
+    ph = np.exp(1j * rng.uniform(0, 2 * np.pi, 2))
+    return {
+        "general": u,
+        "diag": np.diag(ph),
+        "phase": np.diag([1, ph[0]]),
+        "antidiag": np.array([[0, ph[0]], [ph[1], 0]]),
+        "x": C.X,
+        "identity": np.eye(2),
+        "h": C.H,
+    }
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n", [1, 2, 5, 11, 14])
+def test_single_gate_every_class_target_and_control_pattern(mode, n):
+    _, dtype, arith = mode
+    rng = np.random.default_rng(100 + n)
+    psi0 = C.random_state(n, seed=n)
+    h = make_state(n, dtype, arith, psi0)
+    want = psi0.copy()
+    try:
+        for t in range(n):
+            others = [q for q in range(n) if q != t]
+            ctl_sets = [()] + [tuple(rng.choice(others, size=m, replace=False)) for m in (1, 2, 3) if m <= len(others)]
+            for ctl in ctl_sets:
+                for name, u in class_matrices(rng).items():
+                    B.sv_apply_gate(h, u, t, ctl)
+                    oracle.apply_gate(want, u, t, ctl)
+        got = B.sv_read_amplitudes(h).astype(np.complex128)
+    finally:
+        B.sv_destroy(h)
+    assert_close(got, want, dtype, f"n={n}")
+
+
+def mixed_circuit(n, rng):
+    gates = []
+    for _ in range(3):
+        gates += C.random_layers(n, 1, rng)
+        if n >= 3:
+            a, b, c = (int(x) for x in rng.choice(n, 3, replace=False))
+            gates.append(C.gate_swap(a, b))
+            gates.append(C.gate_u(C.X, c, (a, b)))                       # Toffoli
+            gates.append(C.gate_u(C.phase(rng.uniform(0, 6)), a, (c,)))   # controlled phase
+            gates.append(C.gate_u(np.diag(np.exp(1j * rng.uniform(0, 6, 2))), b))
+            gates.append(C.gate_u(C.haar_u2(rng), c, tuple(q for q in (a, b) if q != c)))
+    return C.pack(gates)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n", [3, 8, 12, 13, 16, 18])
+@pytest.mark.parametrize("chunk_k", [0, 6, 8])
+def test_fused_circuits_match_oracle(mode, n, chunk_k):
+    _, dtype, arith = mode
+    rng = np.random.default_rng(7 * n + chunk_k)
+    gates = np.concatenate([mixed_circuit(n, rng), C.pack(C.qft(n))])
+    psi0 = C.random_state(n, seed=1000 + n)
+    want = run_oracle(n, gates, psi0)
+    got = run_gpu(n, gates, dtype, arith, psi0, chunk_k=chunk_k)
+    assert_close(got, want, dtype, f"n={n} k={chunk_k}")
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_unfused_sweeps_match_oracle(mode):
+    _, dtype, arith = mode
+    n = 15
+    gates = mixed_circuit(n, np.random.default_rng(3))
+    psi0 = C.random_state(n, seed=5)
+    assert_close(run_gpu(n, gates, dtype, arith, psi0, fusion=0), run_oracle(n, gates, psi0), dtype)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_qft_n20_from_seeded_basis_state(mode):
+    """The QFT workload (n = 20, |x> from seed 1001): oracle and closed form e^{2 pi i x y / 2^n} / 2^{n/2}."""
+    _, dtype, arith = mode
+    w = C.qft_workload(20, seed=1001)
+    got = run_gpu(w.n, w.gates, dtype, arith, x0=w.x0)
+    want = run_oracle(w.n, w.gates, x0=w.x0)
+    assert_close(got, want, dtype, "qft20 vs oracle")
+    y = np.arange(2 ** w.n)
+    closed = np.exp(2j * np.pi * ((w.x0 * y) % 2 ** w.n) / 2 ** w.n) / 2 ** (w.n / 2)
+    assert_close(got, closed, dtype, "qft20 vs closed form")
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_permutation_circuits_are_bit_exact(mode):
+    """X, CNOT, Toffoli and SWAP only move amplitudes: the result equals the oracle's bit for bit."""
+    _, dtype, arith = mode
+    n = 14
+    rng = np.random.default_rng(11)
+    gates = []
+    for _ in range(40):
+        a, b, c = (int(x) for x in rng.choice(n, 3, replace=False))
+        gates += [C.gate_u(C.X, a), C.cnot(a, b), C.gate_u(C.X, c, (a, b)), C.gate_swap(b, c)]
+    gates = C.pack(gates)
+    psi0 = C.random_state(n, seed=2)
+    if dtype == B.SV_C64:
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    want = run_oracle(n, gates, psi0)
+    for fusion in (0, 1):
+        got = run_gpu(n, gates, dtype, arith, psi0, fusion=fusion)
+        assert np.array_equal(got, want)
+
+
+def test_ghz_exact_in_f64_mode():
+    n = 16
+    g = C.pack(C.ghz(n))
+    got = run_gpu(n, g, B.SV_C128, B.SV_ARITH_F64)
+    want = np.zeros(2 ** n, dtype=np.complex128)
+    want[0] = want[-1] = C.SQRT1_2
+    assert np.array_equal(got, want)
+    got = run_gpu(n, g, B.SV_C128, B.SV_ARITH_DF32)
+    assert np.count_nonzero(got) == 2 and abs(got[0] - C.SQRT1_2) < 4e-15 and got[0] == got[-1]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_graph_replay_and_determinism(mode):
+    _, dtype, arith = mode
+    n = 17
+    gates = C.random_workload(n, 4, seed=21).gates
+    a = run_gpu(n, gates, dtype, arith)
+    b = run_gpu(n, gates, dtype, arith)
+    assert np.array_equal(a, b)
+    h = make_state(n, dtype, arith)
+    try:
+        for rep in range(3):
+            B.sv_init_basis(h, 0)
+            B.sv_apply_circuit_graph(h, gates)
+            assert np.array_equal(B.sv_read_amplitudes(h).astype(np.complex128), a)
+    finally:
+        B.sv_destroy(h)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_norm_probabilities_and_readout(mode):
+    _, dtype, arith = mode
+    n = 19
+    w = C.qft_random_workload(n, 2, seed=4)
+    want = run_oracle(n, w.gates, x0=w.x0)
+    h = make_state(n, dtype, arith, x0=w.x0)
+    try:
+        B.sv_apply_circuit(h, w.gates)
+        assert abs(B.sv_norm(h) - oracle.norm2(want)) < (1e-13 if dtype == B.SV_C128 else 1e-5)
+        p = B.sv_read_probabilities(h, 5, 1000)
+        tol = 1e-13 if dtype == B.SV_C128 else 1e-6 * np.max(oracle.probabilities(want))
+        assert np.max(np.abs(p - oracle.probabilities(want)[5:1005])) <= tol
+        idx = np.random.default_rng(1).integers(0, 2 ** n, 5000)
+        assert_close(B.sv_read_amplitudes_at(h, idx).astype(np.complex128), want[idx], dtype, "gather")
+        part = B.sv_read_amplitudes(h, 777, 3333).astype(np.complex128)
+        assert_close(part, want[777:777 + 3333], dtype, "range read")
+        layout = B.sv_get_layout(h)
+        B.sv_canonicalize(h)
+        assert list(B.sv_get_layout(h)) == list(range(n))
+        assert_close(B.sv_read_amplitudes(h).astype(np.complex128), want, dtype, f"canonical (layout was {layout})")
+        # renormalisation divides by the norm
+        B.sv_renormalize(h)
+        assert abs(B.sv_norm(h) - 1.0) < (1e-13 if dtype == B.SV_C128 else 1e-5)
+    finally:
+        B.sv_destroy(h)
+
+
+def test_buffer_state_over_torch_tensor_stays_in_logical_order():
+    torch = pytest.importorskip("torch")
+    n = 15
+    psi0 = C.random_state(n, seed=9)
+    t = torch.from_numpy(psi0).to("cuda")
+    torch.cuda.synchronize()
+    h = B.sv_create_from_buffer(n, B.SV_C128, t.data_ptr())
+    try:
+        w = C.pack(C.qft(n))
+        B.sv_apply_circuit(h, w)
+        B.sv_sync(h)
+        want = run_oracle(n, w, psi0)
+        assert_close(t.cpu().numpy(), want, B.SV_C128, "tensor contents")
+    finally:
+        B.sv_destroy(h)
+
+
+def test_host_validation_leaves_state_untouched():
+    n = 6
+    h = make_state(n, B.SV_C128, B.SV_ARITH_DF32, x0=5)
+    try:
+        before = B.sv_read_amplitudes(h)
+        bad = C.pack([C.gate_u(C.H, 0), C.gate_u(C.X, 9)])
+        with pytest.raises(B.SvError) as e:
+            B.sv_apply_circuit(h, bad)
+        assert e.value.code == B.SV_ERR_ARG and "gate 1" in str(e.value)
+        with pytest.raises(B.SvError) as e:
+            B.sv_apply_gate(h, np.array([[1, 1], [0, 1]]), 0)
+        assert e.value.code == B.SV_ERR_NOT_UNITARY
+        assert np.array_equal(B.sv_read_amplitudes(h), before)
+    finally:
+        B.sv_destroy(h)
+
+
+def test_oversized_state_is_refused():
+    with pytest.raises(B.SvError) as e:
+        B.sv_create(36, B.SV_C128)
+    assert e.value.code == B.SV_ERR_OOM
