@@ -164,6 +164,25 @@ sv_status sv_read_probabilities(sv_state *s, uint64_t first, uint64_t count, dou
 /* sum_k |alpha_k|^2 accumulated in (at least) double precision.  Synchronises. */
 sv_status sv_norm(sv_state *s, double *out);
 
+/* Norm without any device allocation.  The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory themselves, e.g. a host framework that has already reserved the
+ * GPU's memory for its own pool (so a cudaMalloc here would fail or fragment that pool), or a latency-critical
+ * loop that cannot afford cudaMalloc's implicit device synchronisation.  They keep ownership of every buffer:
+ *   psi    device pointer to 2^n amplitudes of `dtype` in physical order (16-byte aligned); the norm does not
+ *          depend on the order
+ *   d_out  device pointer to one double that receives sum_k |alpha_k|^2 (8-byte aligned)
+ *   stream cudaStream_t or NULL; the work is queued on it and the call returns without waiting
+ * The per-block partial sums go to a fixed scratch array of SV_NORM_NOALLOC_MAX_PARTIALS doubles (32 KiB)
+ * compiled into the library: every GPU that loads the library keeps it until the process exits.  The first
+ * call on a device does a one-time set-up (it looks up that array's device address, with the device
+ * current); make that first call on each device before any stream capture.  Every call writes
+ * each partial it later reads, so nothing needs clearing between calls, but all calls share the one array:
+ * calls whose work overlaps on the GPU (e.g. on two streams) race and give wrong results.
+ * Errors: SV_ERR_ARG (NULL or misaligned pointer, n outside [1, 36], bad dtype, or a GPU whose partial-sum
+ * count exceeds SV_NORM_NOALLOC_MAX_PARTIALS), SV_ERR_NO_DEVICE, SV_ERR_CUDA.  No allocation on any path. */
+#define SV_NORM_NOALLOC_MAX_PARTIALS 4096
+sv_status sv_norm_noalloc(const void *psi, int n, sv_dtype dtype, void *stream, double *d_out);
+
 /* Divide every amplitude by sqrt(sum |alpha_k|^2). */
 sv_status sv_renormalize(sv_state *s);
 

@@ -44,7 +44,7 @@ SV_GATE_SWAP = 1
 EXPORTED = [
     "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_write_amplitudes", "sv_set_option",
     "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_swap", "sv_apply_circuit",
-    "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_norm",
+    "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version",
 ]
@@ -89,6 +89,7 @@ def load(path: str | None = None):
         "sv_read_amplitudes_at": [P, P, u64, P],
         "sv_read_probabilities": [P, u64, u64, P],
         "sv_norm": [P, ctypes.POINTER(d)],
+        "sv_norm_noalloc": [P, i, i, P, P],
         "sv_renormalize": [P],
         "sv_sync": [P],
         "sv_last_plan_stats": [P, P, P, P, P, P],
@@ -238,6 +239,12 @@ def sv_norm(h: int) -> float:
     v = ctypes.c_double()
     _check(load().sv_norm(h, ctypes.byref(v)))
     return v.value
+
+
+def sv_norm_noalloc(psi_ptr: int, n: int, dtype: int, d_out_ptr: int, stream=None) -> None:
+    """Queue the norm of the 2^n amplitudes at device address psi_ptr into the double at device address
+    d_out_ptr, using only the library's fixed scratch array (no allocation)."""
+    _check(load().sv_norm_noalloc(psi_ptr, n, dtype, _stream_ptr(stream), d_out_ptr))
 
 
 def sv_renormalize(h: int) -> None:
