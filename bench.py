@@ -60,7 +60,14 @@ def parse():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--no-f64", action="store_true", help="skip the native-FP64 context measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default chunk size")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--workload", choices=["random", "batched", "served"], default="random",
+                    help="random: the headline n=30 circuit; batched: 4096 circuits in one sv_run_batch call; "
+                         "served: Poisson request stream through the serving loop")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--served-rates", default="10,30,100", help="request rates (per s) to sweep")
+    ap.add_argument("--served-count", type=int, default=200, help="requests per rate")
     return ap.parse_args()
 
 
@@ -248,11 +255,23 @@ def run_ours(args):
         amps = B.sv_read_amplitudes(h, 0, READ_COUNT)
         return nrm, amps
 
+    # Chunk size per dtype from the autotuner, timed on a 4-layer circuit of the same shape (untimed here).
+    chunk_k, tuning = {}, {}
+    if not args.no_autotune:
+        from paper_1801_01037_gb300 import autotune
+        probe = C.random_workload(args.n, 4, seed=SEED + 7).gates
+        for dt, ar in ((B.SV_C128, B.SV_ARITH_DF32), (B.SV_C64, B.SV_ARITH_AUTO)):
+            res = autotune.tune(args.n, dt, probe, ar, save=False)
+            chunk_k[dt] = res["best"]
+            tuning["c128" if dt == B.SV_C128 else "c64"] = res
+
     def timed(dtype, arith, steps, warmup, profile=False, sampler=None):
         h = B.sv_create(args.n, dtype)
         try:
             if dtype == B.SV_C128:
                 B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            if dtype in chunk_k:
+                B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k[dtype])
             B.sv_set_option(h, B.SV_OPT_PROFILE, 1 if profile else 0)
             for _ in range(warmup):
                 step(h)
@@ -281,6 +300,30 @@ def run_ours(args):
         finally:
             B.sv_destroy(h)
 
+    def sweep_roofline(dtype, arith, u, label, peak):
+        """Single-gate sweeps (the unfused path) on targets spread over all qubits, timed per launch."""
+        h = B.sv_create(args.n, dtype)
+        try:
+            if dtype == B.SV_C128:
+                B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            B.sv_set_option(h, B.SV_OPT_PROFILE, 1)
+            targets = sorted({0, 1, args.n // 4, args.n // 2, 3 * args.n // 4, args.n - 2, args.n - 1})
+            for t in targets[:2]:
+                B.sv_apply_gate(h, u, t)
+            ms_list = []
+            for t in targets:
+                B.sv_apply_gate(h, u, t)
+                _, ms = B.sv_profile_last(h, 1)
+                ms_list.append(ms)
+            ab = (8 if dtype == B.SV_C64 else 16) << args.n
+            avg = sum(ms_list) / len(ms_list)
+            ach = 2 * ab / (avg * 1e-3) / 1e9
+            return {"kernel": f"k_sweep ({label})", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "avg_launch_ms": avg, "algorithmic_bytes_per_launch": 2 * ab,
+                    "targets": targets, "per_target_ms": [round(x, 3) for x in ms_list]}
+        finally:
+            B.sv_destroy(h)
+
     sampler = ClockSampler()
     c128 = timed(B.SV_C128, B.SV_ARITH_DF32, args.steps, args.warmup, profile=True, sampler=sampler)
     c64 = timed(B.SV_C64, B.SV_ARITH_AUTO, args.steps, args.warmup)
@@ -289,6 +332,8 @@ def run_ours(args):
     # end to end through the public API with host buffers: gate records uploaded and results read every step
     h = B.sv_create(args.n, B.SV_C128)
     try:
+        if B.SV_C128 in chunk_k:
+            B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k[B.SV_C128])
         for _ in range(max(1, args.warmup)):
             step(h, graph=False)
         torch.cuda.synchronize()
@@ -311,8 +356,18 @@ def run_ours(args):
     state_bytes = 16 << args.n
 
     peak, peak_kind = measured_peaks()
+    u_dense = C.haar_u2(np.random.Generator(np.random.PCG64(7)))
+    sweeps = [sweep_roofline(B.SV_C128, B.SV_ARITH_DF32, u_dense, "c128 dense U(2), double-float", peak),
+              sweep_roofline(B.SV_C128, B.SV_ARITH_DF32, C.X, "c128 X, moves", peak),
+              sweep_roofline(B.SV_C64, B.SV_ARITH_AUTO, u_dense, "c64 dense U(2)", peak)]
     avg_ms = c128["fused_ms"] / max(1, c128["fused_launches"])
-    achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9 if c128["fused_launches"] else None
+    hbm_achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9 if c128["fused_launches"] else None
+    # FP32-pipe roofline of the fused pass (it is bound by instruction issue, not by HBM).
+    ops_step = df32_ops_per_step(gates, args.n, c128["stats"]["passes"])
+    ops_launch = ops_step / max(1, c128["stats"]["passes"])
+    sm_hz = (c128["clocks"] or {}).get("sm_mhz") or 2070.0
+    alu_peak = 152 * 128 * sm_hz * 1e6 / 1e12
+    alu_achieved = ops_launch / (avg_ms * 1e-3) / 1e12 if c128["fused_launches"] else None
     traffic = committed_traffic()
     launches_per_step = 1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
@@ -332,7 +387,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32x2 (double-float) arithmetic on IEEE-double complex128 storage",
         "data": "synthetic (seeded Haar-random U(2) layers and random-matching CNOTs)",
-        "config": workload_config(args),
+        "config": {**workload_config(args),
+                   "chunk_qubits": {"c128": chunk_k.get(B.SV_C128, "default 12"), "c64": chunk_k.get(B.SV_C64, "default 13")},
+                   "autotune_ms": tuning},
         "effective_hbm_gbs": value * 2 * state_bytes / 1e9 / WORLD,
         "c64": {"value": total_gates / c64_t, "unit": "gates/s",
                 "ms_per_step": c64_t * 1e3 / args.steps,
@@ -341,20 +398,56 @@ def run_ours(args):
                                                  "ms_per_step": f64["ms"], "note": "c128 with FP64 arithmetic, 1 step"},
         "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
                  "fused_gates_per_step": c128["stats"]["fused_gates"]},
-        "roofline": {"kernel": "k_fused<c128 df32> (fused chunk pass)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": 2 * state_bytes, "avg_launch_ms": avg_ms,
-                     "launches_timed": c128["fused_launches"], "peak_source": f"{peak_kind} hbm_gbs"},
+        "roofline": {"kernel": "k_fused<c128, double-float> (fused chunk pass)", "bound": "alu",
+                     "achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
+                     "frac": (alu_achieved / alu_peak) if alu_achieved else None, "traffic": traffic,
+                     "algorithmic_ops_per_launch": ops_launch, "avg_launch_ms": avg_ms,
+                     "launches_timed": c128["fused_launches"],
+                     "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
+                     "hbm_view": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": (hbm_achieved / peak) if hbm_achieved else None,
+                                  "algorithmic_bytes_per_launch": 2 * state_bytes,
+                                  "peak_source": f"{peak_kind} hbm_gbs"}},
+        "sweep_roofline": sweeps,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "gates/s",
-                "h2d_bytes_per_step": st["fused_gates"] * 192 + st["sweep_gates"] * 0,
-                "d2h_bytes_per_step": 8 + READ_COUNT * 16},
+                "h2d_bytes_per_step": st["fused_gates"] * 224,
+                "d2h_bytes_per_step": 8 + READ_COUNT * 16,
+                "note": "h2d: planned gate records (208 B) plus group descriptors (16 B), upper bound per gate"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": c128["clocks"],
         "norm_last_step": c128["norm"],
     }
     print(json.dumps(line), flush=True)
+
+
+# FP32-pipe operations of the double-float method per amplitude (integer, float add/sub, FMA and conversion
+# instructions each count one): a dense 2x2 update (four 4-term compensated dot products: 6 per term, 7 per
+# TwoSum step, 3 for the final Fast2Sum, i.e. 48 per real output), a complex scaling (diagonal / anti-diagonal
+# entries, two 2-term dot products), and the double <-> float-pair conversion once per pass at load and store.
+DF32_OPS_DENSE = 96
+DF32_OPS_SCALE = 44
+DF32_OPS_CONVERT = 68
+
+
+def df32_ops_per_step(gates, n, passes):
+    """Algorithmic FP32-pipe operations of one application of `gates` with `passes` fused passes."""
+    ops = float(passes) * DF32_OPS_CONVERT * 2 ** n
+    for g in gates:
+        if int(g["kind"]) != C.GATE_U:
+            continue
+        u = C.unpack_u(g)
+        touched = 2.0 ** (n - int(g["ncontrols"]))
+        if u[0, 1] == 0 and u[1, 0] == 0:
+            if u[0, 0] == 1 and u[1, 1] == 1:
+                continue
+            ops += DF32_OPS_SCALE * touched * (0.5 if u[0, 0] == 1 else 1.0)
+        elif u[0, 0] == 0 and u[1, 1] == 0:
+            if not (u[0, 1] == 1 and u[1, 0] == 1):
+                ops += DF32_OPS_SCALE * touched
+        else:
+            ops += DF32_OPS_DENSE * touched
+    return ops
 
 
 def committed_traffic():
@@ -374,10 +467,105 @@ def committed_traffic():
         return None
 
 
+def run_batched(args):
+    """4096 independent random circuits (n log-uniform in [10, 22], 10-40 layers, seed 1004) in one
+    sv_run_batch call per dtype; the call plans, allocates, uploads, runs and synchronises."""
+    import torch
+    from paper_1801_01037_gb300 import build as sv_build
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    import oracle
+    B.load()
+    ws = C.batched_workloads(args.batch_count, seed=1004)
+    ns, gl = [w.n for w in ws], [w.gates for w in ws]
+    gates_total = sum(len(g) for g in gl)
+    amps_total = sum(2 ** n for n in ns)
+    res = {}
+    for dt, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
+        for h in B.sv_run_batch(ns[:64], dt, gl[:64]):  # warm-up: kernels, allocator
+            B.sv_destroy(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = B.sv_run_batch(ns, dt, gl)
+        dt_s = time.perf_counter() - t0
+        # check a sample of the small circuits against the oracle
+        err = 0.0
+        for i in [i for i in range(len(ws)) if ns[i] <= 12][:8]:
+            want = oracle.simulate(ns[i], gl[i])
+            got = B.sv_read_amplitudes(hs[i]).astype(np.complex128)
+            err = max(err, float(np.max(np.abs(got - want))))
+        for h in hs:
+            B.sv_destroy(h)
+        res[name] = {"seconds": dt_s, "circuits_per_s": len(ws) / dt_s, "gates_per_s": gates_total / dt_s,
+                     "max_abs_err_sampled_vs_oracle": err}
+    print(json.dumps({"metric": "batched random circuits: circuits/s (one sv_run_batch call, end to end)",
+                      "workload": f"{len(ws)} circuits, n log-uniform in [10, 22], depth 10-40 layers, seed 1004",
+                      "gates": gates_total, "amplitudes": amps_total, **res}), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals through the serving loop (150 GB budget), complex64; per rate: circuits/s and
+    latency percentiles (completion seen by sv_poll minus scheduled arrival)."""
+    import threading
+    import torch
+    from paper_1801_01037_gb300 import build as sv_build
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    B.load()
+    torch.cuda.init()
+    sweep = []
+    for rate in [float(x) for x in args.served_rates.split(",")]:
+        stream = C.served_stream(args.served_count, rate, seed=1005)
+        srv = B.sv_server_create(150 * 10 ** 9, 512)
+        tickets, arrival, done_at = [], {}, {}
+        lock = threading.Lock()
+        finished = threading.Event()
+
+        def poller():
+            while not finished.is_set() or len(done_at) < len(stream):
+                with lock:
+                    pending = [t for t in tickets if t not in done_at]
+                for t in pending:
+                    d, h = B.sv_poll(srv, t)
+                    if d:
+                        done_at[t] = time.perf_counter()
+                        B.sv_destroy(h)
+                if len(done_at) == len(stream):
+                    break
+                time.sleep(0.0002)
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for at, w in stream:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            t = B.sv_submit(srv, w.n, B.SV_C64, w.gates)
+            with lock:
+                tickets.append(t)
+                arrival[t] = t0 + at
+        finished.set()
+        th.join()
+        t_end = max(done_at.values())
+        lat = np.array([(done_at[t] - arrival[t]) * 1e3 for t in tickets])
+        B.sv_server_destroy(srv)
+        sweep.append({"rate_per_s": rate, "requests": len(stream), "circuits_per_s": len(stream) / (t_end - t0),
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "mean_ms": float(lat.mean())})
+    print(json.dumps({"metric": "served circuits/s and p50/p99 latency (complex64, 150 GB budget, continuous batching)",
+                      "workload": "Poisson arrivals; each request a random circuit with n log-uniform in [12, 28], "
+                                  "10-30 layers, seed 1005", "sweep": sweep}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -224,6 +224,36 @@ def qft_random_workload(n: int = 33, depth: int = 10, seed: int = 1003) -> Workl
     return Workload(f"qft_random_n{n}_d{depth}", n, x, pack(qft(n) + random_layers(n, depth, rng)))
 
 
+def random_layers_packed(n: int, depth: int, rng: np.random.Generator) -> np.ndarray:
+    """The same layer structure as :func:`random_layers`, drawn in bulk and packed directly (batched QR for the
+    Haar unitaries), for workloads with millions of gates.  Per layer: n U(2) records, then n // 2 CNOTs."""
+    per = n + n // 2
+    out = np.zeros(depth * per, dtype=GATE_DTYPE)
+    z = (rng.standard_normal((depth, n, 2, 2)) + 1j * rng.standard_normal((depth, n, 2, 2))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    u = q * (d / np.abs(d))[..., None, :]
+    flat = np.stack([u.real, u.imag], axis=-1).reshape(depth, n, 8)
+    xrec = _pack_u(X)
+    for L in range(depth):
+        base = L * per
+        blk = out[base:base + n]
+        blk["U"] = flat[L]
+        blk["target"] = np.arange(n)
+        blk["target2"] = -1
+        blk["controls"] = -1
+        perm = rng.permutation(n)
+        c = out[base + n:base + per]
+        c["U"] = xrec
+        c["target"] = perm[1:2 * (n // 2):2]
+        c["target2"] = -1
+        c["ncontrols"] = 1
+        ctl = np.full((n // 2, MAX_CONTROLS), -1, dtype=np.int32)
+        ctl[:, 0] = perm[0:2 * (n // 2):2]
+        c["controls"] = ctl
+    return out
+
+
 def batched_workloads(count: int = 4096, n_lo: int = 10, n_hi: int = 22, d_lo: int = 10, d_hi: int = 40,
                       seed: int = 1004) -> list:
     """``count`` independent random circuits; n = round(exp(U(ln n_lo, ln n_hi))), depth uniform in
@@ -233,7 +263,8 @@ def batched_workloads(count: int = 4096, n_lo: int = 10, n_hi: int = 22, d_lo: i
     ds = rng.integers(d_lo, d_hi + 1, size=count)
     out = []
     for i in range(count):
-        out.append(Workload(f"b{i}_n{ns[i]}_d{ds[i]}", int(ns[i]), 0, pack(random_layers(int(ns[i]), int(ds[i]), rng))))
+        out.append(Workload(f"b{i}_n{ns[i]}_d{ds[i]}", int(ns[i]), 0,
+                            random_layers_packed(int(ns[i]), int(ds[i]), rng)))
     return out
 
 
@@ -248,7 +279,7 @@ def served_stream(count: int, rate_hz: float, n_lo: int = 12, n_hi: int = 28, d_
     out = []
     for i in range(count):
         out.append((float(t[i]), Workload(f"s{i}_n{ns[i]}_d{ds[i]}", int(ns[i]), 0,
-                                          pack(random_layers(int(ns[i]), int(ds[i]), rng)))))
+                                          random_layers_packed(int(ns[i]), int(ds[i]), rng))))
     return out
 
 

@@ -45,8 +45,10 @@ typedef enum { SV_C64 = 1, SV_C128 = 2 } sv_dtype;
  *   SV_ARITH_AUTO  : SV_ARITH_DF32 for complex128, FP32 for complex64 (the default).
  *   SV_ARITH_F64   : native FP64 multiply-adds (exact IEEE double, about 1/70 of the FP32 rate on GB300).
  *   SV_ARITH_DF32  : each double is split into a pair of floats (hi + lo, >= 47 significant bits) with
- *                    integer bit operations, the 2x2 product is a compensated float dot product, and the
- *                    result is re-assembled into a double; relative error per gate <= 2^-44.
+ *                    integer bit operations, each output of the 2x2 product is a compensated float dot
+ *                    product (exact products by FMA, TwoSum accumulation) with the gate entries split exactly
+ *                    into three floats, and the result is re-assembled into a double.  Error per gate: a few
+ *                    2^-47 of the largest term (absolute), i.e. ~1e-14 for amplitudes of order 1.
  * complex64 states always use FP32 arithmetic. */
 typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_F64 = 1, SV_ARITH_DF32 = 2 } sv_arith;
 

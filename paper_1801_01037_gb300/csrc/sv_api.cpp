@@ -1,6 +1,7 @@
 // C ABI: handles, host-side validation, planning and launch of the kernels.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -64,10 +65,9 @@ PlanConfig plan_config(const sv_state *s) {
   return c;
 }
 
-int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<DevGate> &b, DevGate **d_a,
-                 DevGate **d_b) {
-  const size_t total = a.size() + b.size();
-  *d_a = *d_b = nullptr;
+int upload_plan(sv_state *s, const Plan &P, void **d_blob) {
+  const size_t total = plan_blob_bytes(P);
+  *d_blob = nullptr;
   if (total == 0) return SV_OK;
   cudaError_t e;
   if (s->stage_pending) {
@@ -80,8 +80,8 @@ int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<D
       cudaFree(s->d_gates);
       s->d_gates = nullptr;
     }
-    const size_t cap = std::max<size_t>(total, 256);
-    if ((e = cudaMalloc(&s->d_gates, cap * sizeof(DevGate))) != cudaSuccess) {
+    const size_t cap = std::max<size_t>(total, 64 << 10);
+    if ((e = cudaMalloc(&s->d_gates, cap)) != cudaSuccess) {
       s->d_gates_cap = 0;
       return set_error(SV_ERR_OOM, "device gate buffer allocation failed");
     }
@@ -90,22 +90,19 @@ int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<D
   if (total > s->h_stage_cap) {
     if (s->h_stage) cudaFreeHost(s->h_stage);
     s->h_stage = nullptr;
-    const size_t cap = std::max<size_t>(total, 256);
-    if ((e = cudaMallocHost(&s->h_stage, cap * sizeof(DevGate))) != cudaSuccess) {
+    const size_t cap = std::max<size_t>(total, 64 << 10);
+    if ((e = cudaMallocHost(&s->h_stage, cap)) != cudaSuccess) {
       s->h_stage_cap = 0;
       return set_error(SV_ERR_OOM, "pinned gate staging allocation failed");
     }
     s->h_stage_cap = cap;
   }
-  if (!a.empty()) std::memcpy(s->h_stage, a.data(), a.size() * sizeof(DevGate));
-  if (!b.empty()) std::memcpy(s->h_stage + a.size(), b.data(), b.size() * sizeof(DevGate));
-  if ((e = cudaMemcpyAsync(s->d_gates, s->h_stage, total * sizeof(DevGate), cudaMemcpyHostToDevice, s->stream)) !=
-      cudaSuccess)
+  plan_blob_fill(P, s->h_stage);
+  if ((e = cudaMemcpyAsync(s->d_gates, s->h_stage, total, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
     return cuda_fail(e, "gate upload");
   if ((e = cudaEventRecord(s->stage_ev, s->stream)) != cudaSuccess) return cuda_fail(e, "event record");
   s->stage_pending = true;
-  *d_a = s->d_gates;
-  *d_b = s->d_gates + a.size();
+  *d_blob = s->d_gates;
   return SV_OK;
 }
 
@@ -135,7 +132,7 @@ std::vector<int> step_kinds(const Plan &P) {
   return k;
 }
 
-int run_plan(sv_state *s, const Plan &P, DevGate *d_fused, DevGate *, cudaStream_t st, const cudaEvent_t *evs,
+int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st, const cudaEvent_t *evs,
              bool capturing) {
   const int mode = mode_of(s);
   const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -147,7 +144,7 @@ int run_plan(sv_state *s, const Plan &P, DevGate *d_fused, DevGate *, cudaStream
     if (step.kind == Step::FUSED) {
       PassDesc d = P.passes[step.index];
       d.psi = s->psi;
-      d.gates = d_fused + P.pass_gate_offset[step.index];
+      plan_pass_pointers(P, step.index, d_blob, d);
       // A pass of pure exchanges (X / CNOT / Toffoli) moves doubles as they are: bit-exact in every mode.
       bool moves_only = mode == MODE_C128_DF32;
       for (int i = 0; moves_only && i < d.ngates; ++i)
@@ -181,6 +178,9 @@ int canonicalize_now(sv_state *s) {
 
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero) {
   const size_t bytes = amp_bytes(dt) << n;
+  // Host-side failure injection for tests: with SV_FAULT_ALLOC set, every state allocation fails as if
+  // the device were out of memory (nothing is launched, the GPU is not touched).
+  if (std::getenv("SV_FAULT_ALLOC")) return set_error(SV_ERR_OOM, "allocation failure injected (SV_FAULT_ALLOC)");
   size_t free_b = 0, total_b = 0;
   cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
@@ -298,7 +298,6 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       return SV_OK;
     case SV_OPT_CHUNK_QUBITS:
       if (value != 0 && (value < 6 || value > kMaxChunkQubits)) return set_error(SV_ERR_ARG, "chunk qubits must be 0 or 6..13");
-      if (value > 12 && s->dtype == SV_C128) return set_error(SV_ERR_ARG, "complex128 chunks are at most 2^12 amplitudes");
       s->chunk_k = (int)value;
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
@@ -344,8 +343,8 @@ static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool 
   if (single) cfg.fusion = false;
   Plan P;
   make_plan(s->n, cfg, s->perm, gates, ngates, P);
-  DevGate *d_fused = nullptr, *d_sweep = nullptr;
-  int rc = upload_gates(s, P.fused_gates, {}, &d_fused, &d_sweep);
+  void *d_blob = nullptr;
+  int rc = upload_plan(s, P, &d_blob);
   if (rc != SV_OK) return rc;
   const cudaEvent_t *evs = nullptr;
   s->last_evs = nullptr;
@@ -356,7 +355,7 @@ static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool 
     s->last_evs = evs;
     s->last_kind = step_kinds(P);
   }
-  rc = run_plan(s, P, d_fused, d_sweep, s->stream, evs, false);
+  rc = run_plan(s, P, d_blob, s->stream, evs, false);
   if (rc != SV_OK) return rc;
   s->st_passes = (int)P.passes.size();
   s->st_fused = P.n_fused_gates;

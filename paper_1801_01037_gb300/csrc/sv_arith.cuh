@@ -66,40 +66,56 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (qh + ql)(xh + xl): returns the rounded product qh*xh and adds its exact rounding error plus the two
-// cross terms to c (the ql*xl term is below 2^-48 relative and dropped).
-__device__ __forceinline__ float df_prod(float qh, float ql, dfv x, float &c) {
+// Dot products of double-float numbers (a compensated dot product in the manner of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005).  Each product qh*xh is split exactly into p + e by one multiply and
+// one FMA; the p's are summed with TwoSum (Knuth), whose exact rounding errors, the e's and the cross terms
+// qh*xl, qm*xh and ql*xh of the three-float gate entry q = qh + qm + ql go to a float accumulator c (the terms
+// with xl times qm or ql are below 2^-48 relative and dropped; they depend on the amplitude, so they average
+// out, whereas an error in q itself would bias every amplitude the same way).  c carries about 2^-23 of the
+// result, so its own rounding leaves an error of a few 2^-47 of the largest term.  A final Fast2Sum
+// renormalises the pair (|c| <= |s| except under cancellation, where the error stays that small in absolute
+// terms).
+__device__ __forceinline__ float df_term(float qh, float qm, float ql, dfv x, float &c) {
   const float p = __fmul_rn(qh, x.h);
   c = __fadd_rn(c, __fmaf_rn(qh, x.h, -p));
   c = __fmaf_rn(qh, x.l, c);
+  c = __fmaf_rn(qm, x.h, c);
   c = __fmaf_rn(ql, x.h, c);
   return p;
 }
 
-// sum of four double-float products, renormalised with TwoSum.
-__device__ __forceinline__ dfv df_dot4(float q0h, float q0l, dfv x0, float q1h, float q1l, dfv x1,
-                                       float q2h, float q2l, dfv x2, float q3h, float q3l, dfv x3) {
-  float c = 0.0f, s, e;
-  const float p0 = df_prod(q0h, q0l, x0, c);
-  const float p1 = df_prod(q1h, q1l, x1, c);
-  const float p2 = df_prod(q2h, q2l, x2, c);
-  const float p3 = df_prod(q3h, q3l, x3, c);
-  two_sum(p0, p1, s, e); c = __fadd_rn(c, e);
-  two_sum(s, p2, s, e); c = __fadd_rn(c, e);
-  two_sum(s, p3, s, e); c = __fadd_rn(c, e);
+__device__ __forceinline__ dfv fast_two_sum(float s, float c) {
   dfv r;
-  two_sum(s, c, r.h, r.l);
+  r.h = __fadd_rn(s, c);
+  r.l = __fsub_rn(c, __fsub_rn(r.h, s));
   return r;
 }
 
-__device__ __forceinline__ dfv df_dot2(float q0h, float q0l, dfv x0, float q1h, float q1l, dfv x1) {
+// A gate entry in three-float form.
+struct q3 { float h, m, l; };
+
+__device__ __forceinline__ dfv df_dot4(q3 q0, dfv x0, q3 q1, dfv x1, q3 q2, dfv x2, q3 q3_, dfv x3) {
   float c = 0.0f, s, e;
-  const float p0 = df_prod(q0h, q0l, x0, c);
-  const float p1 = df_prod(q1h, q1l, x1, c);
-  two_sum(p0, p1, s, e); c = __fadd_rn(c, e);
-  dfv r;
-  two_sum(s, c, r.h, r.l);
-  return r;
+  const float p0 = df_term(q0.h, q0.m, q0.l, x0, c);
+  const float p1 = df_term(q1.h, q1.m, q1.l, x1, c);
+  const float p2 = df_term(q2.h, q2.m, q2.l, x2, c);
+  const float p3 = df_term(q3_.h, q3_.m, q3_.l, x3, c);
+  two_sum(p0, p1, s, e);
+  c = __fadd_rn(c, e);
+  two_sum(s, p2, s, e);
+  c = __fadd_rn(c, e);
+  two_sum(s, p3, s, e);
+  c = __fadd_rn(c, e);
+  return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ dfv df_dot2(q3 q0, dfv x0, q3 q1, dfv x1) {
+  float c = 0.0f, s, e;
+  const float p0 = df_term(q0.h, q0.m, q0.l, x0, c);
+  const float p1 = df_term(q1.h, q1.m, q1.l, x1, c);
+  two_sum(p0, p1, s, e);
+  c = __fadd_rn(c, e);
+  return fast_two_sum(s, c);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -110,7 +126,7 @@ template <int MODE> struct Arith;
 // Coefficients of one gate in the working precision of a mode, loaded once per gate.
 struct CoefF32 { float q[8]; };
 struct CoefF64 { double q[8]; };
-struct CoefDF { float h[8], l[8]; };
+struct CoefDF { float h[8], m[8], l[8]; };
 
 template <> struct Arith<MODE_C64_F32> {
   using G = float2;
@@ -122,7 +138,7 @@ template <> struct Arith<MODE_C64_F32> {
   static __device__ __forceinline__ S one() { return make_float2(1.f, 0.f); }
   static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) c.q[i] = g.qf[i];
+    for (int i = 0; i < 8; ++i) c.q[i] = g.qh[i];
   }
   // r = q[j] * a   (q[j] = complex entry j of the matrix: 0 = q11, 1 = q12, 2 = q21, 3 = q22)
   static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
@@ -181,22 +197,23 @@ template <> struct Arith<MODE_C128_DF32> {
   static __device__ __forceinline__ S one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) { c.h[i] = g.qh[i]; c.l[i] = g.ql[i]; }
+    for (int i = 0; i < 8; ++i) { c.h[i] = g.qh[i]; c.m[i] = g.qm[i]; c.l[i] = g.ql[i]; }
   }
+  // Entry e of the matrix (0 = q11 re, 1 = q11 im, ..., 7 = q22 im), optionally negated.
+  static __device__ __forceinline__ q3 e(const Coef &c, int i) { return q3{c.h[i], c.m[i], c.l[i]}; }
+  static __device__ __forceinline__ q3 ne(const Coef &c, int i) { return q3{-c.h[i], -c.m[i], -c.l[i]}; }
   static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
     const dfv ar{a.x, a.y}, ai{a.z, a.w};
-    const float rh = c.h[2 * j], rl = c.l[2 * j], ih = c.h[2 * j + 1], il = c.l[2 * j + 1];
-    const dfv xr = df_dot2(rh, rl, ar, -ih, -il, ai);
-    const dfv xi = df_dot2(rh, rl, ai, ih, il, ar);
+    const dfv xr = df_dot2(e(c, 2 * j), ar, ne(c, 2 * j + 1), ai);
+    const dfv xi = df_dot2(e(c, 2 * j), ai, e(c, 2 * j + 1), ar);
     return make_float4(xr.h, xr.l, xi.h, xi.l);
   }
   static __device__ __forceinline__ void pair(const Coef &c, S &a, S &b) {
     const dfv ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
-    const float *h = c.h, *l = c.l;
-    const dfv o0r = df_dot4(h[0], l[0], ar, -h[1], -l[1], ai, h[2], l[2], br, -h[3], -l[3], bi);
-    const dfv o0i = df_dot4(h[0], l[0], ai, h[1], l[1], ar, h[2], l[2], bi, h[3], l[3], br);
-    const dfv o1r = df_dot4(h[4], l[4], ar, -h[5], -l[5], ai, h[6], l[6], br, -h[7], -l[7], bi);
-    const dfv o1i = df_dot4(h[4], l[4], ai, h[5], l[5], ar, h[6], l[6], bi, h[7], l[7], br);
+    const dfv o0r = df_dot4(e(c, 0), ar, ne(c, 1), ai, e(c, 2), br, ne(c, 3), bi);
+    const dfv o0i = df_dot4(e(c, 0), ai, e(c, 1), ar, e(c, 2), bi, e(c, 3), br);
+    const dfv o1r = df_dot4(e(c, 4), ar, ne(c, 5), ai, e(c, 6), br, ne(c, 7), bi);
+    const dfv o1i = df_dot4(e(c, 4), ai, e(c, 5), ar, e(c, 6), bi, e(c, 7), br);
     a = make_float4(o0r.h, o0r.l, o0i.h, o0i.l);
     b = make_float4(o1r.h, o1r.l, o1i.h, o1i.l);
   }

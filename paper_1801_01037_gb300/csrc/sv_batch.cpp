@@ -77,7 +77,7 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
     for (sv_state *s : states) if (s) sv_destroy(s);
     return code;
   };
-  size_t total_gates = 0, max_rounds = 0;
+  size_t max_rounds = 0;
   for (int i = 0; i < count; ++i) {
     if ((rc = alloc_state(n[i], dtype, st, &states[i], false)) != SV_OK) {
       const std::string msg = sv_last_error();
@@ -85,17 +85,17 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
       return set_error(rc, "circuit " + std::to_string(i) + ": " + msg);
     }
     plan_fresh(states[i], gates[i], ngates[i], plans[i]);
-    total_gates += plans[i].fused_gates.size();
     max_rounds = std::max(max_rounds, plans[i].passes.size());
   }
-  // Gates of every circuit in one device array; per round, the pass descriptors and chunk prefix sums.
-  std::vector<DevGate> all_gates;
-  all_gates.reserve(total_gates);
-  std::vector<size_t> gate_base(count);
+  // Gates of every circuit in one device blob; per round, the pass descriptors and chunk prefix sums.
+  std::vector<size_t> blob_off(count);
+  size_t blob_bytes = 0;
   for (int i = 0; i < count; ++i) {
-    gate_base[i] = all_gates.size();
-    all_gates.insert(all_gates.end(), plans[i].fused_gates.begin(), plans[i].fused_gates.end());
+    blob_off[i] = blob_bytes;
+    blob_bytes += (plan_blob_bytes(plans[i]) + 15) & ~(size_t)15;
   }
+  std::vector<unsigned char> blob(std::max<size_t>(blob_bytes, 16));
+  for (int i = 0; i < count; ++i) plan_blob_fill(plans[i], blob.data() + blob_off[i]);
   std::vector<PassDesc> descs;
   std::vector<uint64_t> starts;
   struct Round { size_t desc_off, start_off; int npass; uint64_t total; int kmax; };
@@ -106,7 +106,7 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
       if (r >= plans[i].passes.size()) continue;
       PassDesc d = plans[i].passes[r];
       d.psi = states[i]->psi;
-      d.gates = (const DevGate *)(uintptr_t)(gate_base[i] + plans[i].pass_gate_offset[r]);  // offset, fixed below
+      d.init_x = (uint64_t)i;  // circuit index; replaced by the real fields below
       descs.push_back(d);
       starts.push_back(R.total);
       R.total += 1ull << (d.n - d.k);
@@ -117,14 +117,18 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
     rounds.push_back(R);
   }
   DevBuf dg, dd, ds;
-  if (dg.ensure(std::max<size_t>(1, all_gates.size()) * sizeof(DevGate), st) != SV_OK ||
+  if (dg.ensure(blob.size(), st) != SV_OK ||
       dd.ensure(std::max<size_t>(1, descs.size()) * sizeof(PassDesc), st) != SV_OK ||
       ds.ensure(std::max<size_t>(1, starts.size()) * sizeof(uint64_t), st) != SV_OK)
     return cleanup(set_error(SV_ERR_OOM, "batch descriptor allocation failed"));
-  for (PassDesc &d : descs) d.gates = (const DevGate *)dg.p + (uintptr_t)d.gates;
-  cudaError_t e = cudaSuccess;
-  if (!all_gates.empty())
-    e = cudaMemcpyAsync(dg.p, all_gates.data(), all_gates.size() * sizeof(DevGate), cudaMemcpyHostToDevice, st);
+  for (size_t r = 0, di = 0; r < rounds.size(); ++r)
+    for (int i = 0; i < count; ++i) {
+      if (r >= plans[i].passes.size()) continue;
+      PassDesc &d = descs[di++];
+      plan_pass_pointers(plans[i], (int)r, (const unsigned char *)dg.p + blob_off[i], d);
+      d.init_x = plans[i].passes[r].init_x;
+    }
+  cudaError_t e = cudaMemcpyAsync(dg.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ds.p, starts.data(), starts.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   const int mode = default_mode(dtype);
@@ -159,7 +163,7 @@ struct sv_server {
     uint64_t ticket;
     sv_state *st;
     Plan plan;
-    DevGate *d_gates;
+    void *d_gates;   // device blob: the plan's gates
     size_t next;
     size_t bytes;
   };
@@ -200,10 +204,12 @@ struct sv_server {
         continue;
       }
       plan_fresh(a.st, r.gates.data(), r.gates.size(), a.plan);
-      if (!a.plan.fused_gates.empty()) {
-        const size_t gb = a.plan.fused_gates.size() * sizeof(DevGate);
+      if (plan_blob_bytes(a.plan) > 0) {
+        const size_t gb = plan_blob_bytes(a.plan);
+        std::vector<unsigned char> blob(gb);
+        plan_blob_fill(a.plan, blob.data());
         if (cudaMalloc(&a.d_gates, gb) != cudaSuccess ||
-            cudaMemcpyAsync(a.d_gates, a.plan.fused_gates.data(), gb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(a.d_gates, blob.data(), gb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) {
           cudaGetLastError();
           if (a.d_gates) cudaFree(a.d_gates);
@@ -266,7 +272,7 @@ struct sv_server {
         Active &a = active[in_round[j]];
         PassDesc d = a.plan.passes[a.next];
         d.psi = a.st->psi;
-        d.gates = a.d_gates + a.plan.pass_gate_offset[a.next];
+        plan_pass_pointers(a.plan, (int)a.next, a.d_gates, d);
         h_desc[j] = d;
         h_start[j] = total;
         total += 1ull << (d.n - d.k);

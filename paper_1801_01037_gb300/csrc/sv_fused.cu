@@ -17,9 +17,33 @@ namespace svi {
 namespace {
 
 constexpr int kFusedThreads = 256;
+#ifndef SV_FUSED_MIN_BLOCKS
+#define SV_FUSED_MIN_BLOCKS 3
+#endif
 
 __device__ __forceinline__ uint32_t ins0(uint32_t i, int t) {
   return ((i >> t) << (t + 1)) | (i & ((1u << t) - 1u));
+}
+
+#ifndef SV_FUSED_PAIR_UNROLL
+#define SV_FUSED_PAIR_UNROLL 2
+#endif
+constexpr int kPairUnroll = SV_FUSED_PAIR_UNROLL;
+
+// All pairs (j0, j0 | tb) of the chunk for one gate of class CLS, target bit t, local controls cm.
+template <int MODE, int CLS>
+__device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const typename Arith<MODE>::Coef &cf,
+                                            uint32_t half, int t, uint32_t tb, uint32_t cm) {
+  using S = typename Arith<MODE>::S;
+#pragma unroll kPairUnroll
+  for (uint32_t i = threadIdx.x; i < half; i += kFusedThreads) {
+    const uint32_t j0 = ins0(i, t);
+    if ((j0 & cm) != cm) continue;
+    S a = sm[j0], b = sm[j0 | tb];
+    apply_pair<MODE>(CLS, cf, a, b);
+    sm[j0] = a;
+    sm[j0 | tb] = b;
+  }
 }
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64).
@@ -90,13 +114,12 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
           if ((j & cm) == cm) sm[j] = M::cmul(cf, 3, sm[j]);
         }
       } else {
-        for (uint32_t i = tid; i < half; i += kFusedThreads) {
-          const uint32_t j0 = ins0(i, t);
-          if ((j0 & cm) != cm) continue;
-          S a = sm[j0], b = sm[j0 | tb];
-          apply_pair<MODE>(cls, cf, a, b);
-          sm[j0] = a;
-          sm[j0 | tb] = b;
+        // One loop per class, so the class test is not inside the pair loop.
+        switch (cls) {
+          case GC_GENERAL: chunk_pairs<MODE, GC_GENERAL>(sm, cf, half, t, tb, cm); break;
+          case GC_DIAG: chunk_pairs<MODE, GC_DIAG>(sm, cf, half, t, tb, cm); break;
+          case GC_ANTIDIAG: chunk_pairs<MODE, GC_ANTIDIAG>(sm, cf, half, t, tb, cm); break;
+          default: chunk_pairs<MODE, GC_X>(sm, cf, half, t, tb, cm); break;
         }
       }
     } else {
@@ -135,7 +158,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads, 2) k_fused(const PassDesc p, uint64_t nchunks) {
+__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused(const PassDesc p, uint64_t nchunks) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using S = typename Arith<MODE>::S;
   S *sm = (S *)smraw;
@@ -144,7 +167,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused(const PassDesc p, ui
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_batch(const PassDesc *__restrict__ passes,
+__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused_batch(const PassDesc *__restrict__ passes,
                                                                const uint64_t *__restrict__ chunk_start, int npass,
                                                                uint64_t total, int kmax) {
   extern __shared__ __align__(16) unsigned char smraw[];

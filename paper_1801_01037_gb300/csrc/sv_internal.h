@@ -31,9 +31,9 @@ enum GateClass : uint32_t {
 // has target = -1 and its physical target bit in `tmask`.
 struct DevGate {
   double q[8];       // q11, q12, q21, q22 (re, im), FP64
-  float qf[8];       // the same rounded to float (complex64 arithmetic)
-  float qh[8];       // double-float split: q = qh + ql
-  float ql[8];
+  float qh[8];       // q rounded to float (also the complex64 coefficients)
+  float qm[8];       // three-float split q = qh + qm + ql, exact to 2^-72 relative: no systematic
+  float ql[8];       //   coefficient error (a two-float split leaves ~1e-15, e.g. H off unitary by 6e-16)
   uint64_t cmask;
   uint64_t gmask;
   uint64_t tmask;

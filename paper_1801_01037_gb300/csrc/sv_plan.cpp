@@ -28,9 +28,10 @@ int classify(const double *U) {
 void fill_coefficients(DevGate &g, const double *U) {
   for (int i = 0; i < 8; ++i) {
     g.q[i] = U[i];
-    g.qf[i] = (float)U[i];
     g.qh[i] = (float)U[i];
-    g.ql[i] = (float)(U[i] - (double)g.qh[i]);
+    const double r1 = U[i] - (double)g.qh[i];
+    g.qm[i] = (float)r1;
+    g.ql[i] = (float)(r1 - (double)g.qm[i]);
   }
 }
 
@@ -102,6 +103,16 @@ int validate_gate(const sv_gate &g, int n, std::string &why) {
   return SV_OK;
 }
 
+size_t plan_blob_bytes(const Plan &P) { return P.fused_gates.size() * sizeof(DevGate); }
+
+void plan_blob_fill(const Plan &P, void *dst) {
+  if (!P.fused_gates.empty()) std::memcpy(dst, P.fused_gates.data(), P.fused_gates.size() * sizeof(DevGate));
+}
+
+void plan_pass_pointers(const Plan &P, int idx, const void *d_blob, PassDesc &d) {
+  d.gates = (const DevGate *)d_blob + P.pass_gate_offset[idx];
+}
+
 std::vector<std::pair<int, int>> canonicalize_steps(std::vector<int> &perm) {
   std::vector<std::pair<int, int>> out;
   const int n = (int)perm.size();
@@ -120,10 +131,14 @@ namespace {
 
 struct Sched {
   int idx;        // source gate index
-  int cls;
-  int pt;         // physical target
+  int cls;        // gate class, or -2 (SWAP folded into the layout) / -1 (identity): no device work
+  int pt;         // physical target (-1 for SWAP / identity entries)
   uint64_t pc;    // physical control mask
+  uint64_t phys;  // physical bits the entry touches (target, controls; both bits of a SWAP)
+  uint64_t logi;  // logical qubits the entry touches
 };
+
+bool needs_pairing(int cls) { return cls == GC_GENERAL || cls == GC_ANTIDIAG || cls == GC_X; }
 
 DevGate to_sweep_gate(const sv_gate &g, const Sched &s) {
   DevGate d;
@@ -148,11 +163,23 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
 
   auto sched_of = [&](size_t i, int cls) {
     Sched s;
+    const sv_gate &g = gates[i];
     s.idx = (int)i;
     s.cls = cls;
-    s.pt = perm[gates[i].target];
     s.pc = 0;
-    for (int j = 0; j < gates[i].ncontrols; ++j) s.pc |= 1ull << perm[gates[i].controls[j]];
+    s.logi = 1ull << g.target;
+    if (g.kind == SV_GATE_SWAP) {
+      s.pt = -1;
+      s.phys = (1ull << perm[g.target]) | (1ull << perm[g.target2]);
+      s.logi |= 1ull << g.target2;
+      return s;
+    }
+    for (int j = 0; j < g.ncontrols; ++j) {
+      s.pc |= 1ull << perm[g.controls[j]];
+      s.logi |= 1ull << g.controls[j];
+    }
+    s.pt = cls == -1 ? -1 : perm[g.target];
+    s.phys = s.pc | (1ull << perm[g.target]);
     return s;
   };
 
@@ -216,7 +243,6 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
       if (head[u] < q[u].size() && is_ready(q[u][head[u]])) ready.insert(q[u][head[u]]);
     }
   };
-  auto needs_pairing = [](int cls) { return cls == GC_GENERAL || cls == GC_ANTIDIAG || cls == GC_X; };
 
   bool first_pass = true;
   while (!ready.empty() || (first_pass && cfg.init_first)) {
@@ -229,24 +255,24 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
       for (int b = 0; b < c; ++b) inQ[b] = true;
       qcount = c;
     }
-    std::vector<Sched> pg;
+    std::vector<Sched> pg;  // entries of this pass in scheduling order (SWAP / identity entries included)
+    int nreal = 0;
     for (;;) {
       int chosen = -1;
       for (int i : ready) {
         const int cls = cls_of[i];
-        if (cls == -2 || cls == -1) { chosen = i; break; }
-        if (!needs_pairing(cls) || inQ[perm[gates[i].target]]) { chosen = i; break; }
+        if (cls < 0 || !needs_pairing(cls) || inQ[perm[gates[i].target]]) { chosen = i; break; }
       }
       if (chosen >= 0) {
         const int cls = cls_of[chosen];
-        P.gate_order[chosen] = order++;
+        pg.push_back(sched_of(chosen, cls));
         if (cls == -2) {
           std::swap(perm[gates[chosen].target], perm[gates[chosen].target2]);
           ++P.n_relabels;
         } else if (cls == -1) {
           ++P.n_skipped;
         } else {
-          pg.push_back(sched_of(chosen, cls));
+          ++nreal;
         }
         pop(chosen);
         continue;
@@ -265,13 +291,20 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
     }
     const bool init_here = first_pass && cfg.init_first;
     first_pass = false;
-    if (pg.empty() && !init_here) continue;
-    if (pg.size() == 1 && cfg.single_as_sweep && !init_here) {
-      P.gate_step[pg[0].idx] = (int)P.steps.size();
-      P.step_qmask.push_back(1ull << pg[0].pt);
-      P.sweep_gates.push_back(to_sweep_gate(gates[pg[0].idx], pg[0]));
-      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
-      ++P.n_sweep_gates;
+    if (nreal == 0 && !init_here) {
+      for (const Sched &e : pg) P.gate_order[e.idx] = order++;
+      continue;
+    }
+    if (nreal == 1 && cfg.single_as_sweep && !init_here) {
+      for (const Sched &e : pg) {
+        P.gate_order[e.idx] = order++;
+        if (e.cls < 0) continue;
+        P.gate_step[e.idx] = (int)P.steps.size();
+        P.step_qmask.push_back(1ull << e.pt);
+        P.sweep_gates.push_back(to_sweep_gate(gates[e.idx], e));
+        P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+        ++P.n_sweep_gates;
+      }
       continue;
     }
     // Fill Q up to k bits with the lowest unused bits, so every pass has chunks of exactly 2^k amplitudes.
@@ -294,9 +327,13 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
       }
     d.init = init_here ? 1 : 0;
     d.init_x = cfg.init_x;
-    d.ngates = (int)pg.size();
+    const int step_index = (int)P.steps.size();
     P.pass_gate_offset.push_back((int)P.fused_gates.size());
+    int ng = 0;
     for (const Sched &s : pg) {
+      P.gate_order[s.idx] = order++;
+      if (s.cls < 0) continue;
+      P.gate_step[s.idx] = step_index;
       DevGate g;
       std::memset(&g, 0, sizeof g);
       fill_coefficients(g, gates[s.idx].U);
@@ -309,12 +346,13 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
           else g.gmask |= 1ull << b;
         }
       P.fused_gates.push_back(g);
+      ++ng;
     }
-    for (const Sched &s : pg) P.gate_step[s.idx] = (int)P.steps.size();
+    d.ngates = ng;
     P.step_qmask.push_back(d.qmask);
     P.passes.push_back(d);
-    P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, (int)pg.size()});
-    P.n_fused_gates += (int)pg.size();
+    P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, ng});
+    P.n_fused_gates += ng;
   }
 }
 

@@ -38,10 +38,16 @@ struct Plan {
   std::vector<uint64_t> step_qmask;
 };
 
+// The device copy of a plan's fused passes: its DevGates, in one byte blob.
+size_t plan_blob_bytes(const Plan &P);
+void plan_blob_fill(const Plan &P, void *dst);
+// Point pass `idx` of P at its gates inside a device blob that holds plan_blob_fill's bytes.
+void plan_pass_pointers(const Plan &P, int idx, const void *d_blob, PassDesc &d);
+
 // Classify U (8 doubles) by exact comparisons; returns -1 for the identity.
 int classify(const double *U);
 
-// Fill q / qf / qh / ql of a DevGate from U.
+// Fill q / qh / qm / ql of a DevGate from U.
 void fill_coefficients(DevGate &g, const double *U);
 
 // Validate one record against n qubits: qubits in range and distinct, U unitary within 1e-10.

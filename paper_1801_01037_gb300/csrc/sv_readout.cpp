@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "sv_state.h"
 
@@ -192,11 +193,12 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   std::vector<int> perm = s->perm;
   Plan P;
   make_plan(s->n, cfg, perm, gates, ngates, P);
-  if (!P.fused_gates.empty()) {
-    if ((e = cudaMalloc(&ent.d_gates, P.fused_gates.size() * sizeof(DevGate))) != cudaSuccess)
+  if (plan_blob_bytes(P) > 0) {
+    if ((e = cudaMalloc(&ent.d_gates, plan_blob_bytes(P))) != cudaSuccess)
       return set_error(SV_ERR_OOM, "graph gate buffer allocation failed");
-    if ((e = cudaMemcpy(ent.d_gates, P.fused_gates.data(), P.fused_gates.size() * sizeof(DevGate),
-                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+    std::vector<unsigned char> blob(plan_blob_bytes(P));
+    plan_blob_fill(P, blob.data());
+    if ((e = cudaMemcpy(ent.d_gates, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
       cudaFree(ent.d_gates);
       return cuda_fail(e, "graph gate upload");
     }
@@ -225,7 +227,7 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
   int rc = SV_OK;
   if (e == cudaSuccess) {
-    rc = run_plan(s, P, ent.d_gates, nullptr, cap, ent.evs.empty() ? nullptr : ent.evs.data(), true);
+    rc = run_plan(s, P, ent.d_gates, cap, ent.evs.empty() ? nullptr : ent.evs.data(), true);
     if (rc == SV_OK && s->canonical) {
       std::vector<int> pp = perm;
       for (const auto &ab : canonicalize_steps(pp)) {

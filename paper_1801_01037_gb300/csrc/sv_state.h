@@ -11,7 +11,7 @@
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
-  svi::DevGate *d_gates = nullptr;
+  void *d_gates = nullptr;   // device blob: the plan's gates
   std::vector<cudaEvent_t> evs;   // profiling: two events per launch, recorded by the graph itself
   std::vector<int> ev_kind;
   std::vector<int> perm_before, perm_after;
@@ -32,10 +32,10 @@ struct sv_state {
   int64_t renorm_period = 0;
   int64_t gates_since_renorm = 0;
   // device gate buffer and its pinned staging copy
-  svi::DevGate *d_gates = nullptr;
-  size_t d_gates_cap = 0;
-  svi::DevGate *h_stage = nullptr;
-  size_t h_stage_cap = 0;
+  void *d_gates = nullptr;   // device blob of the last plan's gates
+  size_t d_gates_cap = 0;    // bytes
+  void *h_stage = nullptr;   // pinned staging copy of that blob
+  size_t h_stage_cap = 0;    // bytes
   cudaEvent_t stage_ev = nullptr;
   bool stage_pending = false;
   // norm scratch: norm_parts() partials + 1 result
@@ -61,12 +61,11 @@ int mode_of(const sv_state *s);
 size_t amp_bytes(sv_dtype dt);
 int check_device();
 PlanConfig plan_config(const sv_state *s);
-// Upload DevGates through the state's pinned staging buffer into its device gate buffer.
-int upload_gates(sv_state *s, const std::vector<DevGate> &a, const std::vector<DevGate> &b, DevGate **d_a,
-                 DevGate **d_b);
+// Upload the plan's gates through the state's pinned staging buffer into its device blob.
+int upload_plan(sv_state *s, const Plan &P, void **d_blob);
 // Launch the steps of a plan (gates already on the device at d_fused / d_sweep) on stream st.
 // evs: nullptr, or two timing events per step recorded around each launch (external records when capturing).
-int run_plan(sv_state *s, const Plan &P, DevGate *d_fused, DevGate *d_sweep, cudaStream_t st,
+int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st,
              const cudaEvent_t *evs = nullptr, bool capturing = false);
 // Make sure the state's event pool holds at least 2 * steps events.
 int ensure_event_pool(sv_state *s, size_t steps);

@@ -37,3 +37,21 @@ def test_inverse_round_trip_of_records():
 def test_batched_sizes_within_bounds():
     ws = C.batched_workloads(64, seed=1004)
     assert all(10 <= w.n <= 22 for w in ws)
+
+
+def test_bulk_layers_have_the_layer_structure():
+    rng = np.random.Generator(np.random.PCG64(5))
+    n, depth = 7, 4
+    g = C.random_layers_packed(n, depth, rng)
+    assert len(g) == depth * (n + n // 2)
+    per = n + n // 2
+    for L in range(depth):
+        ones = g[L * per:L * per + n]
+        assert list(ones["target"]) == list(range(n)) and np.all(ones["ncontrols"] == 0)
+        for r in ones:
+            u = C.unpack_u(r)
+            assert np.max(np.abs(u.conj().T @ u - np.eye(2))) < 1e-14
+        cn = g[L * per + n:(L + 1) * per]
+        qubits = list(cn["target"]) + list(cn["controls"][:, 0])
+        assert len(set(qubits)) == 2 * (n // 2) and np.all(cn["ncontrols"] == 1)
+        assert all(np.array_equal(C.unpack_u(r), C.X) for r in cn)
