@@ -78,6 +78,11 @@ typedef struct sv_server sv_server;
                                    sv_create_from_buffer states), 0 = keep the relabelled layout lazily */
 #define SV_OPT_PROFILE 6        /* 1 = record a CUDA event before and after every launch of the apply calls
                                    (also inside captured graphs); read them with sv_profile_last */
+#define SV_OPT_F64_SHARE 7      /* complex128 with SV_ARITH_DF32: percent (0..99) of each fused pass's chunks
+                                   computed with native FP64 by one CTA per SM, in parallel with the
+                                   double-float CTAs (the FP64 pipe is otherwise idle); -1 = default (18).
+                                   Which chunks use FP64 depends only on their index: results are
+                                   reproducible run to run. */
 
 /* ---------------------------------------------------------------------------------------------------------
  * States

@@ -3,7 +3,8 @@
 The fused pass holds 2^k amplitudes per CTA in shared memory.  A larger k lets a pass take more gates (fewer
 passes, fewer HBM sweeps) but leaves fewer CTAs per SM to hide each other's load and barrier latency.  This
 module times candidate k on the GPU through the C ABI (``SV_OPT_CHUNK_QUBITS``) for a circuit of the caller's
-shape, keeps the fastest per (n, dtype, arithmetic) in a JSON cache, and applies it to a state.
+shape, then (complex128, double-float) the share of chunks given to the FP64 pipe (``SV_OPT_F64_SHARE``),
+keeps the fastest per (n, dtype, arithmetic) in a JSON cache, and applies it to a state.
 
 Cache file: ``$SV_AUTOTUNE_CACHE`` or ``~/.cache/gb300_statevec_autotune.json``.
 """
@@ -44,12 +45,17 @@ def save_cache(cache: dict) -> None:
     os.replace(tmp, p)
 
 
-def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2) -> float:
-    """Best device time (ms, summed over the fused-pass launches) of one application of `gates` with 2^k chunks."""
+F64_SHARES = (0, 12, 15, 18, 21)
+
+
+def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1) -> float:
+    """Best device time (ms, summed over the fused-pass launches) of one application of `gates` with 2^k chunks
+    (and, for complex128, `f64_share` percent of the chunks in native FP64)."""
     h = B.sv_create(n, dtype)
     try:
         if dtype == B.SV_C128:
             B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            B.sv_set_option(h, B.SV_OPT_F64_SHARE, f64_share)
         B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, k)
         B.sv_set_option(h, B.SV_OPT_PROFILE, 1)
         best = float("inf")
@@ -78,6 +84,10 @@ def tune(n: int, dtype: int, gates, arith: int = B.SV_ARITH_AUTO, candidates=Non
     ms = {k: time_candidate(n, dtype, arith, gates, k) for k in cands}
     best = min(ms, key=ms.get)
     res = {"best": best, "ms": {str(k): v for k, v in ms.items()}}
+    if dtype == B.SV_C128 and arith != B.SV_ARITH_F64:
+        sh = {s: time_candidate(n, dtype, arith, gates, best, f64_share=s) for s in F64_SHARES}
+        res["best_f64_share"] = min(sh, key=sh.get)
+        res["f64_share_ms"] = {str(s): v for s, v in sh.items()}
     if save:
         cache = load_cache()
         cache[_key(n, dtype, arith)] = res
@@ -91,9 +101,13 @@ def best_chunk_qubits(n: int, dtype: int, arith: int = B.SV_ARITH_AUTO) -> int |
 
 
 def apply(h: int, arith: int = B.SV_ARITH_AUTO) -> int | None:
-    """Set the cached best chunk size on state handle `h` (no-op without a cache entry); returns it."""
+    """Set the cached best chunk size (and FP64 share) on state handle `h` (no-op without a cache entry);
+    returns the chunk size."""
     n, dtype, _ = B.sv_get_info(h)
-    k = best_chunk_qubits(n, dtype, arith)
-    if k is not None:
-        B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, k)
-    return k
+    ent = load_cache().get(_key(n, dtype, arith))
+    if not ent:
+        return None
+    B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, int(ent["best"]))
+    if "best_f64_share" in ent:
+        B.sv_set_option(h, B.SV_OPT_F64_SHARE, int(ent["best_f64_share"]))
+    return int(ent["best"])

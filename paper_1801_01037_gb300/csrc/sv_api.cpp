@@ -106,6 +106,8 @@ int upload_plan(sv_state *s, const Plan &P, void **d_blob) {
   return SV_OK;
 }
 
+int f64_share_of(const sv_state *s) { return s->f64_share >= 0 ? s->f64_share : kDefaultF64Share; }
+
 int maybe_renormalize(sv_state *s, int applied) {
   if (s->renorm_period <= 0) return SV_OK;
   s->gates_since_renorm += applied;
@@ -149,7 +151,7 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st, co
       bool moves_only = mode == MODE_C128_DF32;
       for (int i = 0; moves_only && i < d.ngates; ++i)
         moves_only = P.fused_gates[P.pass_gate_offset[step.index] + i].cls == GC_X;
-      e = launch_fused(d, moves_only ? (int)MODE_C128_F64 : mode, st);
+      e = launch_fused(d, moves_only ? (int)MODE_C128_F64 : mode, st, f64_share_of(s), s->d_sched);
     } else if (step.kind == Step::SWEEP) {
       e = launch_sweep(s->psi, s->n, mode, P.sweep_gates[step.index], st);
     } else {
@@ -197,9 +199,11 @@ int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_z
     return set_error(SV_ERR_OOM, "cudaMalloc of the state failed");
   }
   if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
     cudaFree(s->psi);
     if (s->d_scalars) cudaFree(s->d_scalars);
+    if (s->d_sched) cudaFree(s->d_sched);
     delete s;
     return cuda_fail(e, "state scratch allocation");
   }
@@ -250,8 +254,10 @@ sv_status sv_create_from_buffer(int n, sv_dtype dtype, void *dev_ptr, void *stre
   for (int t = 0; t < n; ++t) s->perm[t] = t;
   cudaError_t e;
   if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
     if (s->d_scalars) cudaFree(s->d_scalars);
+    if (s->d_sched) cudaFree(s->d_sched);
     delete s;
     return cuda_fail(e, "state scratch allocation");
   }
@@ -270,6 +276,7 @@ sv_status sv_destroy(sv_state *s) {
   if (s->d_gates) cudaFree(s->d_gates);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->d_scalars) cudaFree(s->d_scalars);
+  if (s->d_sched) cudaFree(s->d_sched);
   if (s->d_read) cudaFree(s->d_read);
   if (s->stage_ev) cudaEventDestroy(s->stage_ev);
   for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
@@ -302,6 +309,10 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
     case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
+    case SV_OPT_F64_SHARE:
+      if (value < -1 || value > 99) return set_error(SV_ERR_ARG, "FP64 share must be -1 (default) or 0..99 percent");
+      s->f64_share = (int)value;
+      return SV_OK;
     case SV_OPT_RENORM_PERIOD:
       if (value < 0) return set_error(SV_ERR_ARG, "renormalisation period must be >= 0");
       s->renorm_period = value;

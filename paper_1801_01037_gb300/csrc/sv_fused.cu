@@ -166,6 +166,48 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused(co
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) fused_chunk<MODE>(p, ch, sm, rowoff);
 }
 
+// Complex128 pass split between the SM's two arithmetic units.  The double-float path keeps the FP32 pipes
+// busy and leaves the FP64 pipe idle; GB300's FP64 pipe is slow (about 1.7 multiply-adds per clock per SM)
+// but independent.  The first CTA to start on each SM (elected through `sched->sm_slot[%smid]`) processes
+// chunks in native FP64, the others in double-float; each role takes its chunks from its own atomic counter.
+// A chunk's arithmetic is fixed by its index (chunk c uses FP64 when c mod 100 < share), so results do not
+// depend on scheduling.  `sched` must be zeroed before the launch.
+__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
+    k_fused_mixed(const PassDesc p, uint64_t nchunks, int share, FusedSched *sched) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int role;
+  __shared__ unsigned long long next;
+  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)16 << p.k));
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    role = atomicAdd(&sched->sm_slot[smid % kSchedSlots], 1u) == 0u ? 1 : 0;
+  }
+  __syncthreads();
+  if (role) {
+    for (;;) {
+      if (threadIdx.x == 0) next = atomicAdd(&sched->next[1], 1ull);
+      __syncthreads();
+      const uint64_t j = next;
+      __syncthreads();
+      const uint64_t c = (j / (uint64_t)share) * 100ull + (j % (uint64_t)share);
+      if (c >= nchunks) break;
+      fused_chunk<MODE_C128_F64>(p, c, (double2 *)smraw, rowoff);
+    }
+  } else {
+    const uint64_t rest = (uint64_t)(100 - share);
+    for (;;) {
+      if (threadIdx.x == 0) next = atomicAdd(&sched->next[0], 1ull);
+      __syncthreads();
+      const uint64_t j = next;
+      __syncthreads();
+      const uint64_t c = (j / rest) * 100ull + (uint64_t)share + (j % rest);
+      if (c >= nchunks) break;
+      fused_chunk<MODE_C128_DF32>(p, c, (float4 *)smraw, rowoff);
+    }
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused_batch(const PassDesc *__restrict__ passes,
                                                                const uint64_t *__restrict__ chunk_start, int npass,
@@ -246,7 +288,28 @@ int fused_smem_bytes(int mode, int k) {
   return mode == MODE_C64_F32 ? smem_bytes<MODE_C64_F32>(k) : smem_bytes<MODE_C128_F64>(k);
 }
 
-cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st) {
+cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_share, FusedSched *sched) {
+  const uint64_t nchunks = 1ull << (p.n - p.k);
+  if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
+    const int smem = smem_bytes<MODE_C128_DF32>(p.k);
+    static int configured = 0;
+    if (smem > configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_fused_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_mixed, kFusedThreads, smem);
+    if (occ < 1) occ = 1;
+    const uint64_t grid = (uint64_t)sms() * occ;
+    // Worth it only with several chunks per CTA and at least two CTAs per SM.
+    if (occ >= 2 && nchunks >= 4 * grid) {
+      cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(FusedSched), st);
+      if (e != cudaSuccess) return e;
+      k_fused_mixed<<<(unsigned)grid, kFusedThreads, smem, st>>>(p, nchunks, f64_share, sched);
+      return cudaGetLastError();
+    }
+  }
   switch (mode) {
     case MODE_C64_F32: return fused_launch<MODE_C64_F32>(p, st);
     case MODE_C128_F64: return fused_launch<MODE_C128_F64>(p, st);

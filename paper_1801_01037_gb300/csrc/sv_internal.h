@@ -63,8 +63,19 @@ static_assert(sizeof(PassDesc) == 88, "PassDesc layout");
 // Kernel launchers (sv_kernels.cu).  All return cudaGetLastError() of the launch.
 // ---------------------------------------------------------------------------------------------------------
 cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream_t st);
+
+// Scratch of the mixed FP64 / double-float pass: one election slot per SM and one chunk counter per role.
+constexpr int kSchedSlots = 256;
+struct FusedSched {
+  unsigned sm_slot[kSchedSlots];
+  unsigned long long next[2];
+};
+
 cudaError_t launch_sweep(void *psi, int n, int mode, const DevGate &g, cudaStream_t st);
-cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st);
+
+// f64_share (complex128 double-float passes only): percent of the chunks done in native FP64 by one CTA per
+// SM alongside the double-float CTAs (0 = all double-float); `sched` is device scratch for that split.
+cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_share = 0, FusedSched *sched = nullptr);
 int fused_smem_bytes(int mode, int k);
 cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st);
 // Logical-order gather: out[i] = psi[phys(idx_i)], idx_i = first + i (d_idx == nullptr) or d_idx[i].

@@ -44,51 +44,59 @@ struct SweepArgs {
 constexpr int kSweepThreads = 256;
 constexpr int kSweepUnroll = 4;
 
-// One gate over the whole state (Algorithm 1, Sec. V.B): each item is a pair (k, k + 2^t) with bit t of k
-// zero and all control bits one.  Items are numbered by the remaining free bits, so consecutive threads
-// touch consecutive addresses whenever the target and controls are not among the lowest index bits.
+// One tile (kSweepThreads * kSweepUnroll items starting at `base`) of a single-gate sweep.  Each item is a pair
+// (k, k + 2^t) with bit t of k zero and all control bits one (Algorithm 1, Sec. V.B); items are numbered by
+// the remaining free bits, so consecutive threads touch consecutive addresses whenever the target and
+// controls are not among the lowest index bits.  All loads of the tile are issued before any arithmetic.
 template <int MODE, int CLS>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(typename Arith<MODE>::G *__restrict__ psi, const SweepArgs a) {
+__device__ __forceinline__ void sweep_tile(typename Arith<MODE>::G *__restrict__ psi, const SweepArgs &a,
+                                           const typename Arith<MODE>::Coef &c, uint64_t base) {
   using M = Arith<MODE>;
   using G = typename M::G;
-  typename M::Coef c;
-  if (CLS != GC_X) M::coef(c, a.g);
   const uint64_t tstride = 1ull << a.g.target;
-  const uint64_t tile = (uint64_t)kSweepThreads * kSweepUnroll;
-  for (uint64_t base = (uint64_t)blockIdx.x * tile; base < a.nitems; base += (uint64_t)gridDim.x * tile) {
-    uint64_t k0[kSweepUnroll];
-    G va[kSweepUnroll], vb[kSweepUnroll];
+  uint64_t k0[kSweepUnroll];
+  G va[kSweepUnroll], vb[kSweepUnroll];
 #pragma unroll
-    for (int u = 0; u < kSweepUnroll; ++u) {
-      const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
-      k0[u] = insert_zeros(i, a.pos, a.npos) | a.setmask;
-      if (i < a.nitems) {
-        if (CLS == GC_PHASE) {
-          vb[u] = psi[k0[u]];
-        } else {
-          va[u] = psi[k0[u]];
-          vb[u] = psi[k0[u] + tstride];
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kSweepUnroll; ++u) {
-      const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
-      if (i >= a.nitems) continue;
-      if (CLS == GC_X) {
-        psi[k0[u]] = vb[u];
-        psi[k0[u] + tstride] = va[u];
-      } else if (CLS == GC_PHASE) {
-        psi[k0[u]] = M::store(M::cmul(c, 3, M::load(vb[u])));
+  for (int u = 0; u < kSweepUnroll; ++u) {
+    const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
+    k0[u] = insert_zeros(i, a.pos, a.npos) | a.setmask;
+    if (i < a.nitems) {
+      if (CLS == GC_PHASE) {
+        vb[u] = psi[k0[u]];
       } else {
-        auto x = M::load(va[u]);
-        auto y = M::load(vb[u]);
-        apply_pair<MODE>(CLS, c, x, y);
-        psi[k0[u]] = M::store(x);
-        psi[k0[u] + tstride] = M::store(y);
+        va[u] = psi[k0[u]];
+        vb[u] = psi[k0[u] + tstride];
       }
     }
   }
+#pragma unroll
+  for (int u = 0; u < kSweepUnroll; ++u) {
+    const uint64_t i = base + (uint64_t)u * kSweepThreads + threadIdx.x;
+    if (i >= a.nitems) continue;
+    if (CLS == GC_X) {
+      psi[k0[u]] = vb[u];
+      psi[k0[u] + tstride] = va[u];
+    } else if (CLS == GC_PHASE) {
+      psi[k0[u]] = M::store(M::cmul(c, 3, M::load(vb[u])));
+    } else {
+      auto x = M::load(va[u]);
+      auto y = M::load(vb[u]);
+      apply_pair<MODE>(CLS, c, x, y);
+      psi[k0[u]] = M::store(x);
+      psi[k0[u] + tstride] = M::store(y);
+    }
+  }
+}
+
+// One gate over the whole state, tiles strided over the grid.
+template <int MODE, int CLS>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(typename Arith<MODE>::G *__restrict__ psi, const SweepArgs a) {
+  using M = Arith<MODE>;
+  typename M::Coef c;
+  if (CLS != GC_X) M::coef(c, a.g);
+  const uint64_t tile = (uint64_t)kSweepThreads * kSweepUnroll;
+  for (uint64_t base = (uint64_t)blockIdx.x * tile; base < a.nitems; base += (uint64_t)gridDim.x * tile)
+    sweep_tile<MODE, CLS>(psi, a, c, base);
 }
 
 template <int MODE, int CLS>

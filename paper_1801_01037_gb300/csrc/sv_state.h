@@ -29,6 +29,7 @@ struct sv_state {
   int chunk_k = 0;            // 0 = default
   int fusion = 1;
   int canonical = 0;
+  int f64_share = -1;         // -1 = library default (SV_OPT_F64_SHARE)
   int64_t renorm_period = 0;
   int64_t gates_since_renorm = 0;
   // device gate buffer and its pinned staging copy
@@ -40,6 +41,7 @@ struct sv_state {
   bool stage_pending = false;
   // norm scratch: norm_parts() partials + 1 result
   double *d_scalars = nullptr;
+  svi::FusedSched *d_sched = nullptr;  // scratch of the mixed FP64 / double-float pass
   // read-out staging (device)
   void *d_read = nullptr;
   size_t d_read_cap = 0;
@@ -71,6 +73,9 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st,
 int ensure_event_pool(sv_state *s, size_t steps);
 std::vector<int> step_kinds(const Plan &P);
 int canonicalize_now(sv_state *s);
+// Percent of complex128 double-float chunks done in native FP64 alongside (see SV_OPT_F64_SHARE).
+constexpr int kDefaultF64Share = 18;
+int f64_share_of(const sv_state *s);
 int maybe_renormalize(sv_state *s, int applied);
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero);
 

@@ -233,3 +233,24 @@ def test_oversized_state_is_refused():
     with pytest.raises(B.SvError) as e:
         B.sv_create(36, B.SV_C128)
     assert e.value.code == B.SV_ERR_OOM
+
+
+@pytest.mark.parametrize("share", [0, 20, 50])
+def test_fp64_share_of_double_float_pass(share):
+    """Complex128 double-float passes with part of the chunks done in native FP64 (SV_OPT_F64_SHARE): the result
+    matches the oracle, and which chunks use FP64 depends only on their index (bit-identical reruns)."""
+    import os as _os
+    n = 23  # enough chunks (2^11 of 2^12 amplitudes) for the split to be used
+    w = C.random_workload(n, 3, seed=31)
+    want = oracle.apply_circuit(oracle.basis_state(n, 0), w.gates, threads=_os.cpu_count() or 1)
+    outs = []
+    for rep in range(2):
+        h = make_state(n, B.SV_C128, B.SV_ARITH_DF32)
+        try:
+            B.sv_set_option(h, B.SV_OPT_F64_SHARE, share)
+            B.sv_apply_circuit(h, w.gates)
+            outs.append(B.sv_read_amplitudes(h).astype(np.complex128))
+        finally:
+            B.sv_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+    assert_close(outs[0], want, B.SV_C128, f"share={share}")
