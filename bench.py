@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--no-f64", action="store_true", help="skip the native-FP64 context measurement")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default chunk size")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
-    ap.add_argument("--workload", choices=["random", "batched", "served"], default="random",
+    ap.add_argument("--workload", choices=["random", "batched", "served", "qft20", "qft33"], default="random",
                     help="random: the headline n=30 circuit; batched: 4096 circuits in one sv_run_batch call; "
-                         "served: Poisson request stream through the serving loop")
+                         "served: Poisson request stream through the serving loop; qft20 / qft33: the QFT "
+                         "configurations (n = 20; n = 33 followed by 10 random layers)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--served-rates", default="10,30,100", help="request rates (per s) to sweep")
     ap.add_argument("--served-count", type=int, default=200, help="requests per rate")
@@ -379,7 +380,7 @@ def run_ours(args):
     f64_fma_launch = f64_fmas_per_step(gates, args.n) * (f64_share / 100.0) / max(1, c128["stats"]["passes"])
     f64_peak = 152 * 1.73 * sm_hz * 1e6 / 1e12  # measured FP64 multiply-adds per clock per SM
     f64_achieved = f64_fma_launch / (avg_ms * 1e-3) / 1e12 if c128["fused_launches"] else None
-    traffic = committed_traffic()
+    traffic = committed_traffic(args.n)
     launches_per_step = 1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
 
@@ -484,9 +485,10 @@ def f64_fmas_per_step(gates, n):
     return f
 
 
-def committed_traffic():
-    """DRAM bytes per launch of the fused c128 pass from the committed ncu summary, if it still matches the
-    kernel source (null otherwise)."""
+def committed_traffic(n):
+    """DRAM bytes per launch of the fused c128 pass on n qubits, scaled from the committed ncu capture (a pass
+    reads and writes the whole state once, so traffic is proportional to 2^n), if that capture still matches
+    the kernel source (null otherwise)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "fused_c128_df32_traffic.txt")
     try:
@@ -496,9 +498,48 @@ def committed_traffic():
             h.update(open(os.path.join(ROOT, "paper_1801_01037_gb300", "csrc", f), "rb").read())
         if kv.get("source_sha256") != h.hexdigest()[:16]:
             return None
-        return float(kv["bytes_per_full_launch"])
+        return float(kv["bytes_per_full_launch_n27"]) * 2.0 ** (n - 27)
     except Exception:
         return None
+
+
+def run_single_config(args):
+    """The other single-state configurations, complex128, default options (autotuned chunk size not applied):
+    qft20 = QFT on n = 20 from a seeded basis state (seed 1001, 16 MiB state, L2-resident: launch overhead and
+    graph replay matter); qft33 = QFT on n = 33 then 10 random layers (seed 1003, 128 GiB state)."""
+    import torch
+    from paper_1801_01037_gb300 import build as sv_build
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    B.load()
+    w = C.qft_workload(20, seed=1001) if args.workload == "qft20" else C.qft_random_workload(33, 10, seed=1003)
+    h = B.sv_create(w.n, B.SV_C128)
+    try:
+        def step():
+            B.sv_init_basis(h, w.x0)
+            B.sv_apply_circuit_graph(h, w.gates)
+            B.sv_norm(h)
+            B.sv_read_amplitudes(h, 0, READ_COUNT)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = B.sv_last_plan_stats(h)
+    finally:
+        B.sv_destroy(h)
+    G = len(w.gates)
+    print(json.dumps({"metric": f"gates/s, {w.name}, complex128", "value": G / (ms / 1e3), "unit": "gates/s",
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "gates": G, "n": w.n,
+                      "effective_hbm_gbs": G / (ms / 1e3) * 2 * (16 << w.n) / 1e9,
+                      "plan": {"passes": st["passes"], "sweeps": st["sweep_gates"], "relabels": st["relabels"]},
+                      "step": "init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back"}),
+          flush=True)
 
 
 def run_batched(args):
@@ -600,6 +641,8 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload in ("qft20", "qft33"):
+        run_single_config(args)
     else:
         run_ours(args)
 

@@ -168,6 +168,17 @@ sv_status sv_read_amplitudes_at(sv_state *s, const uint64_t *idx, uint64_t count
 /* |alpha_k|^2 (Sec. II.A) for k = first..first+count-1, in double precision, to host memory. */
 sv_status sv_read_probabilities(sv_state *s, uint64_t first, uint64_t count, double *host_out);
 
+/* Measurement in the computational basis (the probabilities |alpha_k|^2 of Sec. II.A, normalised by their
+ * sum).  The caller draws the random numbers: u[i] (host, count entries, each in [0, 1)) selects outcome
+ * out[i] = the smallest logical index k with P_0 + ... + P_k > u[i], where P_j = |alpha_j|^2 / sum |alpha|^2
+ * accumulated in FP64 in logical index order.  The state is not collapsed.  Synchronises.
+ * Errors: SV_ERR_ARG (NULL, u outside [0, 1), zero state), SV_ERR_OOM, SV_ERR_CUDA. */
+sv_status sv_sample(sv_state *s, const double *u, uint64_t count, uint64_t *out);
+
+/* Expectation of the Pauli-Z product on the logical qubits set in `mask`:
+ * sum_k |alpha_k|^2 (-1)^popcount(k & mask), accumulated like sv_norm (not divided by the norm).  Synchronises. */
+sv_status sv_expect_z(sv_state *s, uint64_t mask, double *out);
+
 /* sum_k |alpha_k|^2 accumulated in (at least) double precision.  Synchronises. */
 sv_status sv_norm(sv_state *s, double *out);
 

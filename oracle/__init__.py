@@ -127,5 +127,22 @@ def probabilities(psi: np.ndarray) -> np.ndarray:
     return psi.real * psi.real + psi.imag * psi.imag
 
 
+def sample(psi: np.ndarray, u) -> np.ndarray:
+    """Measurement outcomes for uniform numbers u in [0, 1): the smallest index k whose cumulative probability
+    (|alpha_0|^2 + ... + |alpha_k|^2, FP64, index order) exceeds u times the total."""
+    c = np.cumsum(probabilities(psi))
+    return np.searchsorted(c, np.asarray(u, dtype=np.float64) * c[-1], side="right").astype(np.uint64)
+
+
+def expect_z(psi: np.ndarray, mask: int) -> float:
+    """sum_k |alpha_k|^2 (-1)^popcount(k & mask): the Pauli-Z product on the qubits in `mask`."""
+    k = np.arange(psi.size, dtype=np.uint64) & np.uint64(mask)
+    par = np.zeros(psi.size, dtype=np.uint64)
+    while np.any(k):
+        par ^= k & np.uint64(1)
+        k >>= np.uint64(1)
+    return float(np.sum(probabilities(psi) * (1.0 - 2.0 * par)))
+
+
 def max_threads() -> int:
     return int(_load().oracle_max_threads())

@@ -45,7 +45,7 @@ SV_GATE_SWAP = 1
 EXPORTED = [
     "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_write_amplitudes", "sv_set_option",
     "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_swap", "sv_apply_circuit",
-    "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_norm", "sv_norm_noalloc",
+    "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version",
 ]
@@ -90,6 +90,8 @@ def load(path: str | None = None):
         "sv_read_amplitudes_at": [P, P, u64, P],
         "sv_read_probabilities": [P, u64, u64, P],
         "sv_norm": [P, ctypes.POINTER(d)],
+        "sv_sample": [P, P, u64, P],
+        "sv_expect_z": [P, u64, ctypes.POINTER(d)],
         "sv_norm_noalloc": [P, i, i, P, P],
         "sv_renormalize": [P],
         "sv_sync": [P],
@@ -234,6 +236,20 @@ def sv_read_probabilities(h: int, first: int = 0, count: int | None = None) -> n
     out = np.empty(count, dtype=np.float64)
     _check(load().sv_read_probabilities(h, first, count, out.ctypes.data))
     return out
+
+
+def sv_sample(h: int, u) -> np.ndarray:
+    """Logical outcome indices for the caller's uniform numbers u (each in [0, 1))."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    out = np.empty(uu.size, dtype=np.uint64)
+    _check(load().sv_sample(h, uu.ctypes.data, uu.size, out.ctypes.data))
+    return out
+
+
+def sv_expect_z(h: int, mask: int) -> float:
+    v = ctypes.c_double()
+    _check(load().sv_expect_z(h, mask, ctypes.byref(v)))
+    return v.value
 
 
 def sv_norm(h: int) -> float:

@@ -87,7 +87,15 @@ cudaError_t launch_probs(const void *psi, int n, int mode, const int *perm, uint
 // Sum of |psi_k|^2: stage 1 writes `nparts` partial sums (as double) to d_partials, stage 2 adds them in a
 // fixed order into *d_out.  nparts must be norm_parts().
 int norm_parts();
-cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st);
+// pmask != 0: sum of (-1)^popcount(k & pmask) |psi_k|^2 over physical k instead (Pauli-Z expectation).
+cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
+                        uint64_t pmask = 0);
+// Sampling: FP64 probability mass of each block of 2^b consecutive logical indices, then one lookup per shot
+// inside its block (d_blk[i] = block, d_resid[i] = mass to skip inside it) -> logical index.
+cudaError_t launch_block_probs(const void *psi, int n, int mode, const int *perm, int b, double *d_out,
+                               cudaStream_t st);
+cudaError_t launch_sample_block(const void *psi, int n, int mode, const int *perm, int b, const uint64_t *d_blk,
+                                const double *d_resid, uint64_t count, uint64_t *d_out, cudaStream_t st);
 cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cudaStream_t st);
 
 // Batched fused pass: `npass` pass descriptors in device memory; block b handles chunk b - chunk_start[p]

@@ -182,28 +182,32 @@ __global__ void k_probs(const G *__restrict__ psi, int n, const Perm pm, uint64_
 constexpr int kNormThreads = 256;
 constexpr int kNormBlocksPerSm = 4;
 
-__device__ __forceinline__ void acc_sq(float &s, float &c, float h, float l) {
-  const float p = __fmul_rn(h, h);
-  float e = __fmaf_rn(h, h, -p);
-  e = __fmaf_rn(2.0f * h, l, e);
+// Adds sg * (h + l)^2 to the double-float accumulator (s, c); sg = +-1 (exact sign flip).
+__device__ __forceinline__ void acc_sq(float &s, float &c, float h, float l, float sg) {
+  const float p = __fmul_rn(h, h) * sg;
+  float e = __fmaf_rn(h * sg, h, -p);
+  e = __fmaf_rn(2.0f * h * sg, l, e);
   float s2, err;
   two_sum(s, p, s2, err);
   s = s2;
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
+// Stage 1 of sum_k (-1)^popcount(k & pmask) |psi_k|^2 over physical indices k (pmask = 0: the norm).
 template <typename G, bool IS_DOUBLE>
-__global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ psi, uint64_t N, double *__restrict__ partials) {
+__global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ psi, uint64_t N, uint64_t pmask,
+                                                        double *__restrict__ partials) {
   float s = 0.f, c = 0.f;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     const G v = psi[i];
+    const float sg = (__popcll(i & pmask) & 1) ? -1.0f : 1.0f;
     if (IS_DOUBLE) {
       const dfv r = df_split((double)v.x), m = df_split((double)v.y);
-      acc_sq(s, c, r.h, r.l);
-      acc_sq(s, c, m.h, m.l);
+      acc_sq(s, c, r.h, r.l, sg);
+      acc_sq(s, c, m.h, m.l, sg);
     } else {
-      acc_sq(s, c, (float)v.x, 0.f);
-      acc_sq(s, c, (float)v.y, 0.f);
+      acc_sq(s, c, (float)v.x, 0.f, sg);
+      acc_sq(s, c, (float)v.y, 0.f, sg);
     }
   }
   __shared__ double red[kNormThreads];
@@ -232,6 +236,65 @@ __global__ void k_scale(G *__restrict__ psi, uint64_t N, const double *__restric
     v.x = (decltype(v.x))((double)v.x * f);
     v.y = (decltype(v.y))((double)v.y * f);
     psi[i] = v;
+  }
+}
+
+// Measurement sampling.  Logical indices are grouped in blocks of 2^b consecutive values; physical index of
+// logical L = phys_hi(L >> b) | phys_lo(L & (2^b - 1)) because the layout map moves each bit independently.
+// Stage 1: one warp per block adds |alpha|^2 (FP64) over the block in logical order.
+template <typename G>
+__global__ void k_block_probs(const G *__restrict__ psi, int n, const Perm pm, int b, uint64_t nblocks,
+                              double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nblocks; j += warps) {
+    const uint64_t hi = logical_to_physical(j << b, n, pm);
+    double acc = 0.0;
+    for (uint32_t l = lane; l < (1u << b); l += 32) {
+      const G v = psi[hi | logical_to_physical(l, b, pm)];
+      const double re = (double)v.x, im = (double)v.y;
+      acc += re * re + im * im;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[j] = acc;
+  }
+}
+
+// Stage 2: one warp per shot walks its block in logical order (32 entries at a time, warp prefix sums) and
+// returns the first index whose running sum exceeds the residual mass `resid` left after the earlier blocks.
+template <typename G>
+__global__ void k_sample_block(const G *__restrict__ psi, int n, const Perm pm, int b,
+                               const uint64_t *__restrict__ blk, const double *__restrict__ resid, uint64_t count,
+                               uint64_t *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
+    const uint64_t j = blk[i];
+    const double r = resid[i];
+    const uint64_t hi = logical_to_physical(j << b, n, pm);
+    double run = 0.0;
+    uint64_t found = ~0ull, last_nonzero = 0;
+    for (uint32_t base = 0; base < (1u << b) && found == ~0ull; base += 32) {
+      const uint32_t l = base + lane;
+      double p = 0.0;
+      if (l < (1u << b)) {
+        const G v = psi[hi | logical_to_physical(l, b, pm)];
+        const double re = (double)v.x, im = (double)v.y;
+        p = re * re + im * im;
+      }
+      double incl = p;
+      for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, p > 0.0 && run + incl > r);
+      const unsigned nz = __ballot_sync(0xffffffffu, p > 0.0);
+      if (nz) last_nonzero = base + 31 - __clz(nz);
+      if (hit) found = base + __ffs(hit) - 1;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    // Rounding can leave r at or above the block's total: take its last non-zero entry.
+    if (lane == 0) out[i] = (j << b) + (found != ~0ull ? found : last_nonzero);
   }
 }
 
@@ -318,16 +381,39 @@ cudaError_t launch_probs(const void *psi, int n, int mode, const int *perm, uint
 
 int norm_parts() { return num_sms() * kNormBlocksPerSm; }
 
-cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st) {
+cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
+                        uint64_t pmask) {
   const int parts = norm_parts();
   const uint64_t N = 1ull << n;
   if (mode == MODE_C64_F32)
-    k_norm1<float2, false><<<parts, kNormThreads, 0, st>>>((const float2 *)psi, N, d_partials);
+    k_norm1<float2, false><<<parts, kNormThreads, 0, st>>>((const float2 *)psi, N, pmask, d_partials);
   else
-    k_norm1<double2, true><<<parts, kNormThreads, 0, st>>>((const double2 *)psi, N, d_partials);
+    k_norm1<double2, true><<<parts, kNormThreads, 0, st>>>((const double2 *)psi, N, pmask, d_partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_norm2<<<1, 32, 0, st>>>(d_partials, parts, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_probs(const void *psi, int n, int mode, const int *perm, int b, double *d_out,
+                               cudaStream_t st) {
+  const Perm pm = make_perm(perm, n);
+  const uint64_t nblocks = 1ull << (n - b);
+  const unsigned grid = grid_for(nblocks * 32, 256);
+  if (mode == MODE_C64_F32) k_block_probs<float2><<<grid, 256, 0, st>>>((const float2 *)psi, n, pm, b, nblocks, d_out);
+  else k_block_probs<double2><<<grid, 256, 0, st>>>((const double2 *)psi, n, pm, b, nblocks, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_block(const void *psi, int n, int mode, const int *perm, int b, const uint64_t *d_blk,
+                                const double *d_resid, uint64_t count, uint64_t *d_out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const Perm pm = make_perm(perm, n);
+  const unsigned grid = grid_for(count * 32, 256);
+  if (mode == MODE_C64_F32)
+    k_sample_block<float2><<<grid, 256, 0, st>>>((const float2 *)psi, n, pm, b, d_blk, d_resid, count, d_out);
+  else
+    k_sample_block<double2><<<grid, 256, 0, st>>>((const double2 *)psi, n, pm, b, d_blk, d_resid, count, d_out);
   return cudaGetLastError();
 }
 

@@ -146,6 +146,72 @@ sv_status sv_norm(sv_state *s, double *out) {
   return e == cudaSuccess ? SV_OK : cuda_fail(e, "norm");
 }
 
+sv_status sv_expect_z(sv_state *s, uint64_t mask, double *out) {
+  if (!s || !out) return set_error(SV_ERR_ARG, "NULL argument");
+  if (s->n < 64 && (mask >> s->n) != 0) return set_error(SV_ERR_ARG, "mask names qubits >= n");
+  uint64_t pmask = 0;  // the same qubits, as physical index bits
+  for (int t = 0; t < s->n; ++t)
+    if (mask >> t & 1ull) pmask |= 1ull << s->perm[t];
+  double *d_out = s->d_scalars + norm_parts();
+  cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream, pmask);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "expectation");
+}
+
+sv_status sv_sample(sv_state *s, const double *u, uint64_t count, uint64_t *out) {
+  if (!s || ((!u || !out) && count)) return set_error(SV_ERR_ARG, "NULL argument");
+  for (uint64_t i = 0; i < count; ++i)
+    if (!(u[i] >= 0.0 && u[i] < 1.0)) return set_error(SV_ERR_ARG, "u[" + std::to_string(i) + "] is not in [0, 1)");
+  if (count == 0) return SV_OK;
+  const int b = s->n < 10 ? s->n : 10;
+  const uint64_t nblocks = 1ull << (s->n - b);
+  double *d_blocks = nullptr;
+  cudaError_t e = cudaMalloc(&d_blocks, nblocks * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SV_ERR_OOM, "sampling scratch allocation failed");
+  }
+  std::vector<double> blocks(nblocks);
+  e = launch_block_probs(s->psi, s->n, mode_of(s), s->perm.data(), b, d_blocks, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(blocks.data(), d_blocks, nblocks * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(d_blocks);
+  if (e != cudaSuccess) return cuda_fail(e, "block probabilities");
+  // Inclusive prefix sums over the blocks (FP64, logical order) and one binary search per shot.
+  for (uint64_t j = 1; j < nblocks; ++j) blocks[j] += blocks[j - 1];
+  const double total = blocks[nblocks - 1];
+  if (!(total > 0.0)) return set_error(SV_ERR_ARG, "the state has zero norm");
+  const uint64_t chunk = std::min<uint64_t>(count, kReadChunk);
+  int rc = ensure_read_buffer(s, chunk * 3 * sizeof(uint64_t));
+  if (rc != SV_OK) return rc;
+  uint64_t *d_blk = (uint64_t *)s->d_read;
+  double *d_res = (double *)(d_blk + chunk);
+  uint64_t *d_out = (uint64_t *)(d_res + chunk);
+  std::vector<uint64_t> blk(chunk);
+  std::vector<double> res(chunk);
+  for (uint64_t off = 0; off < count; off += chunk) {
+    const uint64_t m = std::min(chunk, count - off);
+    for (uint64_t i = 0; i < m; ++i) {
+      const double target = u[off + i] * total;
+      const uint64_t j = (uint64_t)(std::upper_bound(blocks.begin(), blocks.end(), target) - blocks.begin());
+      const uint64_t jj = j < nblocks ? j : nblocks - 1;
+      blk[i] = jj;
+      res[i] = target - (jj > 0 ? blocks[jj - 1] : 0.0);
+    }
+    e = cudaMemcpyAsync(d_blk, blk.data(), m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_res, res.data(), m * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+      e = launch_sample_block(s->psi, s->n, mode_of(s), s->perm.data(), b, d_blk, d_res, m, d_out, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + off, d_out, m * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sampling");
+  }
+  return SV_OK;
+}
+
 sv_status sv_renormalize(sv_state *s) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
   double *d_out = s->d_scalars + norm_parts();
