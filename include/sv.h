@@ -83,6 +83,9 @@ typedef struct sv_server sv_server;
                                    double-float CTAs (the FP64 pipe is otherwise idle); -1 = default (18).
                                    Which chunks use FP64 depends only on their index: results are
                                    reproducible run to run. */
+#define SV_OPT_CUBES 8          /* complex64: 1 = apply runs of gates on at most 4 chunk bits from registers
+                                   (one shared-memory round trip per run), the default; 0 = one
+                                   shared-memory round trip per gate.  Results are identical either way. */
 
 /* ---------------------------------------------------------------------------------------------------------
  * States
@@ -116,7 +119,9 @@ sv_status sv_get_info(sv_state *s, int *n, sv_dtype *dtype, void **dev_ptr);
  * non-sequential storage, Sec. VI.B).  perm must hold n ints. */
 sv_status sv_get_layout(sv_state *s, int *perm);
 
-/* Put the amplitudes back in logical order in device memory (perm = identity) with in-place bit-swap passes. */
+/* Put the amplitudes back in logical order in device memory (perm = identity).  Done with gate-free chunk
+ * passes whose store permutes bits: each pass moves a whole cycle (or a run of one) of the layout's bit
+ * permutation at once, so a random layout of 30 qubits takes about 4 passes over the state. */
 sv_status sv_canonicalize(sv_state *s);
 
 /* ---------------------------------------------------------------------------------------------------------
@@ -208,7 +213,9 @@ sv_status sv_renormalize(sv_state *s);
 sv_status sv_sync(sv_state *s);
 
 /* Planner statistics of the last apply call: passes launched, gates applied inside fused passes, gates
- * applied by single-gate sweeps, SWAPs folded into the layout, bit-swap passes.  Any pointer may be NULL. */
+ * applied by single-gate sweeps, SWAPs folded into the layout, bit-swap passes of the apply call (buffer
+ * states) plus the bit-permutation passes of canonicalisations since the state was created.  Any pointer may
+ * be NULL. */
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
                              int *remaps);
 

@@ -62,6 +62,7 @@ PlanConfig plan_config(const sv_state *s) {
   else { c.k = 12; c.c = 4; }
   if (s->chunk_k > 0) c.k = s->chunk_k;
   c.fusion = s->fusion != 0;
+  c.cubes = s->dtype == SV_C64 && s->cubes != 0;
   return c;
 }
 
@@ -168,14 +169,24 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st, co
   return SV_OK;
 }
 
-int canonicalize_now(sv_state *s) {
-  const auto swaps = canonicalize_steps(s->perm);
-  for (const auto &ab : swaps) {
-    cudaError_t e = launch_remap_swap(s->psi, s->n, mode_of(s), ab.first, ab.second, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "bit-swap pass");
+int canonicalize_on(sv_state *s, std::vector<int> &perm, cudaStream_t st, int *npasses) {
+  // Pure data movement: complex128 passes move doubles untouched (FP64 working form, no conversion).
+  const int mode = mode_of(s) == MODE_C64_F32 ? (int)MODE_C64_F32 : (int)MODE_C128_F64;
+  const std::vector<PassDesc> passes = canonicalize_passes(s->n, plan_config(s), perm);
+  for (PassDesc d : passes) {
+    d.psi = s->psi;
+    cudaError_t e = launch_fused(d, mode, st);
+    if (e != cudaSuccess) return cuda_fail(e, "bit-permutation pass");
   }
-  s->st_remaps += (int)swaps.size();
+  if (npasses) *npasses = (int)passes.size();
   return SV_OK;
+}
+
+int canonicalize_now(sv_state *s) {
+  int np = 0;
+  const int rc = canonicalize_on(s, s->perm, s->stream, &np);
+  s->st_remaps += np;
+  return rc;
 }
 
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero) {
@@ -308,6 +319,7 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       s->chunk_k = (int)value;
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
+    case SV_OPT_CUBES: s->cubes = value ? 1 : 0; return SV_OK;
     case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
     case SV_OPT_F64_SHARE:
       if (value < -1 || value > 99) return set_error(SV_ERR_ARG, "FP64 share must be -1 (default) or 0..99 percent");

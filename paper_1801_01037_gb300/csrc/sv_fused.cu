@@ -20,6 +20,11 @@ constexpr int kFusedThreads = 256;
 #ifndef SV_FUSED_MIN_BLOCKS
 #define SV_FUSED_MIN_BLOCKS 3
 #endif
+#ifndef SV_FUSED_MIN_BLOCKS_C64
+#define SV_FUSED_MIN_BLOCKS_C64 2
+#endif
+template <int MODE>
+constexpr int min_blocks() { return MODE == MODE_C64_F32 ? SV_FUSED_MIN_BLOCKS_C64 : SV_FUSED_MIN_BLOCKS; }
 
 __device__ __forceinline__ uint32_t ins0(uint32_t i, int t) {
   return ((i >> t) << (t + 1)) | (i & ((1u << t) - 1u));
@@ -30,6 +35,23 @@ __device__ __forceinline__ uint32_t ins0(uint32_t i, int t) {
 #endif
 constexpr int kPairUnroll = SV_FUSED_PAIR_UNROLL;
 
+// Shared-memory slot of chunk-local amplitude o.  Complex64 chunks XOR bits 4..6 of the index into bits 1..3,
+// so that the threads of a half-warp, whose register cubes differ in the lowest bits outside the cube, land
+// on distinct banks.  Bit 0 is left alone, so amplitudes 2m and 2m+1 stay adjacent (one 16-byte copy); the
+// map only permutes each aligned group of 128 slots, so it is a bijection for every k.
+template <int MODE>
+__device__ __forceinline__ uint32_t slot(uint32_t o) {
+  if constexpr (MODE == MODE_C64_F32) return o ^ (((o >> 4) & 7u) << 1);
+  else return o;
+}
+
+// 16-byte asynchronous copy global -> shared (no register staging), and the wait for this thread's copies.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // All pairs (j0, j0 | tb) of the chunk for one gate of class CLS, target bit t, local controls cm.
 template <int MODE, int CLS>
 __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const typename Arith<MODE>::Coef &cf,
@@ -39,14 +61,98 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
   for (uint32_t i = threadIdx.x; i < half; i += kFusedThreads) {
     const uint32_t j0 = ins0(i, t);
     if ((j0 & cm) != cm) continue;
-    S a = sm[j0], b = sm[j0 | tb];
+    const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
+    S a = sm[s0], b = sm[s1];
     apply_pair<MODE>(CLS, cf, a, b);
-    sm[j0] = a;
-    sm[j0 | tb] = b;
+    sm[s0] = a;
+    sm[s1] = b;
   }
 }
 
-// Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64).
+// ---- Complex64 register cubes (GC_CUBE) ----------------------------------------------------------------
+// v[s] holds the amplitude whose cube bits spell s (bit i of s = chunk bit pos[i]).  Each routine applies one
+// gate to the 16 registers with the same arithmetic, in the same order, as the shared-memory pair loop, so
+// the two paths give identical results.  cs: the gate's control bits inside the cube, as cube bits.
+using C64 = Arith<MODE_C64_F32>;
+
+template <int J, int CLS>
+__device__ __forceinline__ void cube_pairs(float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (s & (1 << J)) continue;
+    if (((uint32_t)s & cs) != cs) continue;
+    apply_pair<MODE_C64_F32>(CLS, cf, v[s], v[s | (1 << J)]);
+  }
+}
+
+template <int CLS>
+__device__ __forceinline__ void cube_pairs_at(int j, float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
+  switch (j) {
+    case 0: cube_pairs<0, CLS>(v, cf, cs); break;
+    case 1: cube_pairs<1, CLS>(v, cf, cs); break;
+    case 2: cube_pairs<2, CLS>(v, cf, cs); break;
+    default: cube_pairs<3, CLS>(v, cf, cs); break;
+  }
+}
+
+// Diagonal gate whose target bit is the same for all 16 registers (one = that bit).
+__device__ __forceinline__ void cube_diag_uniform(float2 (&v)[16], const CoefF32 &cf, uint32_t cs, bool one,
+                                                  bool phase) {
+  if (!one && phase) return;
+  const int e = one ? 3 : 0;
+  const float qr = e ? cf.q[6] : cf.q[0], qi = e ? cf.q[7] : cf.q[1];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (((uint32_t)s & cs) != cs) continue;
+    v[s] = make_float2(__fmaf_rn(qr, v[s].x, -qi * v[s].y), __fmaf_rn(qr, v[s].y, qi * v[s].x));
+  }
+}
+
+__device__ __forceinline__ uint32_t cube_off(int s, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
+  return ((s & 1) ? m0 : 0u) | ((s & 2) ? m1 : 0u) | ((s & 4) ? m2 : 0u) | ((s & 8) ? m3 : 0u);
+}
+
+// The cube's `cnt` gates over chunk bits packed in `pos`, for every base index of the chunk.
+__device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint32_t pos, uint64_t base, float2 *sm, int k) {
+  const int p0 = pos & 0xff, p1 = (pos >> 8) & 0xff, p2 = (pos >> 16) & 0xff, p3 = (pos >> 24) & 0xff;
+  const uint32_t m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2, m3 = 1u << p3;
+  const uint32_t cube = m0 | m1 | m2 | m3;
+  const uint32_t nbase = 1u << (k - kCubeBits);
+  for (uint32_t bi = threadIdx.x; bi < nbase; bi += kFusedThreads) {
+    const uint32_t bidx = ins0(ins0(ins0(ins0(bi, p0), p1), p2), p3);
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = sm[slot<MODE_C64_F32>(bidx | cube_off(s, m0, m1, m2, m3))];
+    for (int gi = 0; gi < cnt; ++gi) {
+      const DevGate &g = gs[gi];
+      if ((base & g.gmask) != g.gmask) continue;
+      const uint32_t cm = (uint32_t)g.cmask, cb = cm & ~cube;
+      if ((bidx & cb) != cb) continue;
+      const uint32_t cs = ((cm >> p0) & 1u) | (((cm >> p1) & 1u) << 1) | (((cm >> p2) & 1u) << 2) |
+                          (((cm >> p3) & 1u) << 3);
+      const uint32_t cls = g.cls;
+      const int t = g.target;
+      const int j = t == p0 ? 0 : t == p1 ? 1 : t == p2 ? 2 : t == p3 ? 3 : -1;
+      CoefF32 cf;
+      if (cls != GC_X) C64::coef(cf, g);
+      switch (cls) {
+        case GC_GENERAL: cube_pairs_at<GC_GENERAL>(j, v, cf, cs); break;
+        case GC_ANTIDIAG: cube_pairs_at<GC_ANTIDIAG>(j, v, cf, cs); break;
+        case GC_X: cube_pairs_at<GC_X>(j, v, cf, cs); break;
+        default:
+          if (j >= 0 && cls == GC_DIAG) cube_pairs_at<GC_DIAG>(j, v, cf, cs);
+          else if (j >= 0) cube_pairs_at<GC_PHASE>(j, v, cf, cs);
+          else cube_diag_uniform(v, cf, cs, t >= 0 ? ((bidx >> t) & 1u) != 0 : (base & g.tmask) != 0, cls == GC_PHASE);
+          break;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 16; ++s) sm[slot<MODE_C64_F32>(bidx | cube_off(s, m0, m1, m2, m3))] = v[s];
+  }
+}
+
+// Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
+// permuted store's table.
 template <int MODE>
 __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, typename Arith<MODE>::S *sm,
                                             uint64_t *rowoff) {
@@ -70,6 +176,14 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     for (int j = c; j < k; ++j) off |= (uint64_t)((r >> (j - c)) & 1u) << p.qpos[j];
     rowoff[r] = off;
   }
+  // Permuted store: the source slot of output slot o is the bit permutation P(o) = P(o mod 256) | P(o - o mod 256);
+  // the table holds P(i * 256) for the 2^(k-8) values of i.
+  uint32_t *ptab = (uint32_t *)(rowoff + nrows);
+  if (p.permuted && tid < 32u && (tid << 8) < nloc) {
+    uint32_t v = 0;
+    for (int j = 0; j < k; ++j) v |= (((tid << 8) >> p.src_bit[j]) & 1u) << j;
+    ptab[tid] = v;
+  }
   __syncthreads();
 
   G *psi = (G *)p.psi;
@@ -78,21 +192,21 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const bool mine = (p.init_x & ~p.qmask) == base;
     uint32_t lx = 0;
     for (int j = 0; j < k; ++j) lx |= (uint32_t)((p.init_x >> p.qpos[j]) & 1ull) << j;
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads) sm[o] = (mine && o == lx) ? M::one() : M::zero();
+    for (uint32_t o = tid; o < nloc; o += kFusedThreads) sm[slot<MODE>(o)] = (mine && o == lx) ? M::one() : M::zero();
   } else {
-    // Issue four loads before converting, so each thread keeps several requests in flight.
-    for (uint32_t o0 = tid; o0 < nloc; o0 += 4 * kFusedThreads) {
-      G v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t o = o0 + u * kFusedThreads;
-        if (o < nloc) v[u] = psi[base + rowoff[o >> c] + (o & lowmask)];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t o = o0 + u * kFusedThreads;
-        if (o < nloc) sm[o] = M::load(v[u]);
-      }
+    // The whole chunk in flight at once: one 16-byte asynchronous copy per amplitude (complex128) or per
+    // adjacent pair (complex64), straight into its shared-memory slot.  Rows are 2^c >= 2 amplitudes long
+    // and 16-byte aligned, so a pair never straddles two rows.
+    constexpr uint32_t per = 16u / sizeof(G);
+    for (uint32_t u = tid; u < nloc / per; u += kFusedThreads) {
+      const uint32_t o = u * per;
+      cp_async16(&sm[slot<MODE>(o)], &psi[base + rowoff[o >> c] + (o & lowmask)]);
+    }
+    cp_async_wait_all();
+    if constexpr (MODE == MODE_C128_DF32) {
+      // Each thread converts the slots it copied, in place (double2 and the float4 working form are both
+      // 16 bytes), so no barrier is needed before the conversion.
+      for (uint32_t o = tid; o < nloc; o += kFusedThreads) sm[o] = M::load(((const G *)sm)[o]);
     }
   }
   __syncthreads();
@@ -102,6 +216,14 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const uint64_t gmask = g.gmask;
     if ((base & gmask) != gmask) continue;  // a control bit outside the chunk is 0: the gate skips this chunk
     const uint32_t cls = g.cls;
+    if (cls == GC_CUBE) {
+      if constexpr (MODE == MODE_C64_F32) {
+        cube_run(p.gates + gi + 1, g.target, (uint32_t)g.cmask, base, sm, k);
+        gi += g.target;
+        __syncthreads();
+      }
+      continue;  // other modes apply the cube's gates one by one
+    }
     const int t = g.target;
     const uint32_t cm = (uint32_t)g.cmask;
     typename M::Coef cf;
@@ -111,7 +233,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
       if (cls == GC_PHASE) {
         for (uint32_t i = tid; i < half; i += kFusedThreads) {
           const uint32_t j = ins0(i, t) | tb;
-          if ((j & cm) == cm) sm[j] = M::cmul(cf, 3, sm[j]);
+          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
         }
       } else {
         // One loop per class, so the class test is not inside the pair loop.
@@ -127,38 +249,32 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
       const bool one = (base & g.tmask) != 0;
       if (one) {
         for (uint32_t j = tid; j < nloc; j += kFusedThreads)
-          if ((j & cm) == cm) sm[j] = M::cmul(cf, 3, sm[j]);
+          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
       } else if (cls != GC_PHASE) {
         for (uint32_t j = tid; j < nloc; j += kFusedThreads)
-          if ((j & cm) == cm) sm[j] = M::cmul(cf, 0, sm[j]);
+          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 0, sm[slot<MODE>(j)]);
       }
     }
     __syncthreads();
   }
 
   if (!p.permuted) {
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads) psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[o]);
+    for (uint32_t o = tid; o < nloc; o += kFusedThreads)
+      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(o)]);
   } else {
     // Store with chunk-local bit j sent to physical bit qpos_out[j]: output slot o (bits in the ascending
-    // order of Q) takes local amplitude src(o), bit j of src(o) = bit pos(qpos_out[j]) of o.
-    int8_t sp[16];
-    for (int j = 0; j < k; ++j) {
-      int s = 0;
-      for (int i = 0; i < k; ++i)
-        if (p.qpos[i] == p.qpos_out[j]) s = i;
-      sp[j] = (int8_t)s;
-    }
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads) {
-      uint32_t src = 0;
-      for (int j = 0; j < k; ++j) src |= ((o >> sp[j]) & 1u) << j;
-      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[src]);
-    }
+    // order of Q) takes local amplitude P(o), bit j of P(o) = bit src_bit[j] of o.
+    uint32_t plo = 0;
+    for (int j = 0; j < k; ++j) plo |= ((tid >> p.src_bit[j]) & 1u) << j;
+    const uint32_t *ptab = (const uint32_t *)(rowoff + nrows);
+    for (uint32_t o = tid; o < nloc; o += kFusedThreads)
+      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(plo | ptab[o >> 8])]);
   }
   __syncthreads();
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused(const PassDesc p, uint64_t nchunks) {
+__global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused(const PassDesc p, uint64_t nchunks) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using S = typename Arith<MODE>::S;
   S *sm = (S *)smraw;
@@ -209,7 +325,7 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused_batch(const PassDesc *__restrict__ passes,
+__global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused_batch(const PassDesc *__restrict__ passes,
                                                                const uint64_t *__restrict__ chunk_start, int npass,
                                                                uint64_t total, int kmax) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -227,6 +343,18 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS) k_fused_ba
   }
 }
 
+// Largest dynamic shared-memory size already granted to kernel `fn` on the current device; raises it if
+// `bytes` is larger.  One slot per (kernel, device).
+cudaError_t ensure_smem(const void *fn, int bytes, int *granted_per_device) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (bytes <= granted_per_device[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) granted_per_device[dev] = bytes;
+  return e;
+}
+
 int g_sms = 0;
 int sms() {
   if (!g_sms) {
@@ -238,21 +366,19 @@ int sms() {
   return g_sms;
 }
 
-// The planner keeps c >= min(3, k), so the row table never has more than max(1, 2^(k-3)) entries.
+// The planner keeps c >= min(3, k), so the row table never has more than max(1, 2^(k-3)) entries; 128 bytes
+// of permuted-store table follow it.
 template <int MODE>
 int smem_bytes(int k) {
-  return (int)(sizeof(typename Arith<MODE>::S) << k) + (int)(sizeof(uint64_t) << (k > 3 ? k - 3 : 0));
+  return (int)(sizeof(typename Arith<MODE>::S) << k) + (int)(sizeof(uint64_t) << (k > 3 ? k - 3 : 0)) + 128;
 }
 
 template <int MODE>
 cudaError_t fused_launch(const PassDesc &p, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(p.k);
-  static int configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem((const void *)k_fused<MODE>, smem, granted);
+  if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<MODE>, kFusedThreads, smem);
   if (occ < 1) occ = 1;
@@ -267,12 +393,9 @@ template <int MODE>
 cudaError_t fused_batch_launch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
                                int kmax, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(kmax);
-  static int configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_batch<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem((const void *)k_fused_batch<MODE>, smem, granted);
+  if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_batch<MODE>, kFusedThreads, smem);
   if (occ < 1) occ = 1;
@@ -292,12 +415,9 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
   const uint64_t nchunks = 1ull << (p.n - p.k);
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
     const int smem = smem_bytes<MODE_C128_DF32>(p.k);
-    static int configured = 0;
-    if (smem > configured) {
-      cudaError_t e = cudaFuncSetAttribute(k_fused_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      configured = smem;
-    }
+    static int granted[64] = {0};
+    cudaError_t e = ensure_smem((const void *)k_fused_mixed, smem, granted);
+    if (e != cudaSuccess) return e;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_mixed, kFusedThreads, smem);
     if (occ < 1) occ = 1;

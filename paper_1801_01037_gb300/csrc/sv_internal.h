@@ -23,7 +23,15 @@ enum GateClass : uint32_t {
   GC_PHASE = 2,     // diagonal with q11 = 1: only amplitudes whose target bit is 1 change
   GC_ANTIDIAG = 3,  // q11 = q22 = 0: alpha_k <- q12 alpha_{k+2^t}, alpha_{k+2^t} <- q21 alpha_k
   GC_X = 4,         // q12 = q21 = 1, q11 = q22 = 0: the pair is exchanged (pure moves)
+  GC_CUBE = 5,      // not a gate: header of a register cube (complex64 fused passes, see below)
 };
+
+// Register cube.  Inside a complex64 fused pass, a header DevGate with cls = GC_CUBE says that the next
+// `target` gates act only on the four chunk-local bits packed in the low four bytes of `cmask` (ascending),
+// apart from diagonal gates, which may sit on any bit.  Each thread then holds the 16 amplitudes that
+// differ in those four bits in registers and applies all of the cube's gates there: one shared-memory
+// round trip for the run instead of one per gate.
+constexpr int kCubeBits = 4;
 
 // One gate as the kernels see it.  In a single-gate sweep, `target` and `cmask` are physical bits.  Inside
 // a fused pass they are chunk-local bits; controls that lie outside the chunk go to `gmask` (physical bits
@@ -56,8 +64,9 @@ struct PassDesc {
   int8_t qpos_out[16];
   int32_t init;           // 0: read the chunk from HBM; 1: synthesise |init_x> restricted to the chunk
   int32_t permuted;       // 1 if qpos_out differs from qpos
+  int8_t src_bit[16];     // permuted: bit j of the local amplitude stored at slot o is bit src_bit[j] of o
 };
-static_assert(sizeof(PassDesc) == 88, "PassDesc layout");
+static_assert(sizeof(PassDesc) == 104, "PassDesc layout");
 
 // ---------------------------------------------------------------------------------------------------------
 // Kernel launchers (sv_kernels.cu).  All return cudaGetLastError() of the launch.

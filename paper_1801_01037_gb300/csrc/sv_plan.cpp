@@ -127,6 +127,76 @@ std::vector<std::pair<int, int>> canonicalize_steps(std::vector<int> &perm) {
   return out;
 }
 
+std::vector<PassDesc> canonicalize_passes(int n, const PlanConfig &cfg, std::vector<int> &perm) {
+  int c = std::min(cfg.c, n);
+  c = std::max(c, std::min(3, n));
+  // At least two bits besides the low ones, so that every pass puts at least one bit in its place.
+  const int k = std::min(n, std::max(cfg.k, c + 2));
+  std::vector<PassDesc> out;
+  for (int guard = 0; guard <= n; ++guard) {
+    // dest[p]: physical bit that the data now at physical bit p belongs to (logical qubit t sits at perm[t]).
+    int dest[64];
+    bool done = true;
+    for (int t = 0; t < n; ++t) {
+      dest[perm[t]] = t;
+      done = done && perm[t] == t;
+    }
+    if (done) break;
+    // Q: the c low bits, then consecutive runs along the cycles of dest while bits are left.
+    bool inq[64] = {false};
+    int nbits = 0;
+    for (int b = 0; b < c; ++b) { inq[b] = true; ++nbits; }
+    bool seen[64] = {false};
+    for (int b0 = 0; b0 < n && nbits < k; ++b0) {
+      if (seen[b0] || dest[b0] == b0) continue;
+      for (int b = b0; !seen[b]; b = dest[b]) {
+        seen[b] = true;
+        if (!inq[b]) {
+          if (nbits == k) break;
+          inq[b] = true;
+          ++nbits;
+        }
+      }
+    }
+    for (int b = 0; b < n && nbits < k; ++b)
+      if (!inq[b]) { inq[b] = true; ++nbits; }
+    // sigma on Q: a bit whose destination is in Q sends its data there; the remaining ones fill, in order,
+    // the bits of Q that nothing in Q is sent to.  The first kind is final; the pass is a bijection of Q.
+    int sigma[64];
+    bool hit[64] = {false};
+    for (int b = 0; b < n; ++b)
+      if (inq[b] && inq[dest[b]]) { sigma[b] = dest[b]; hit[dest[b]] = true; }
+    int fill = 0;
+    for (int b = 0; b < n; ++b) {
+      if (!inq[b] || inq[dest[b]]) continue;
+      while (!inq[fill] || hit[fill]) ++fill;
+      sigma[b] = fill;
+      hit[fill] = true;
+    }
+    PassDesc d;
+    std::memset(&d, 0, sizeof d);
+    d.n = n;
+    d.k = k;
+    d.c = c;
+    int j = 0;
+    for (int b = 0; b < n; ++b)
+      if (inq[b]) {
+        d.qpos[j] = (int8_t)b;
+        d.qpos_out[j] = (int8_t)sigma[b];
+        d.qmask |= 1ull << b;
+        ++j;
+      }
+    d.permuted = 1;
+    for (int jj = 0; jj < k; ++jj)
+      for (int i = 0; i < k; ++i)
+        if (d.qpos[i] == d.qpos_out[jj]) d.src_bit[jj] = (int8_t)i;
+    out.push_back(d);
+    for (int t = 0; t < n; ++t)
+      if (inq[perm[t]]) perm[t] = sigma[perm[t]];
+  }
+  return out;
+}
+
 namespace {
 
 struct Sched {
@@ -151,6 +221,40 @@ DevGate to_sweep_gate(const sv_gate &g, const Sched &s) {
 }
 
 } // namespace
+
+// Split a pass's gate run (chunk-local targets) into register cubes, in order: a cube takes gates while the
+// distinct targets of its pairing gates stay within kCubeBits bits; diagonal gates join any cube.  Unused
+// cube bits are filled from the top of the chunk, which keeps the threads of a half-warp on distinct
+// shared-memory banks for most bit sets.
+void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out) {
+  size_t i = 0;
+  while (i < run.size()) {
+    uint32_t bits = 0;
+    int nb = 0;
+    size_t j = i;
+    for (; j < run.size(); ++j) {
+      const DevGate &g = run[j];
+      if (!needs_pairing((int)g.cls) || g.target < 0) continue;
+      const uint32_t tb = 1u << g.target;
+      if (bits & tb) continue;
+      if (nb == kCubeBits) break;
+      bits |= tb;
+      ++nb;
+    }
+    for (int b = k - 1; b >= 0 && nb < kCubeBits; --b)
+      if (!(bits >> b & 1u)) { bits |= 1u << b; ++nb; }
+    DevGate h;
+    std::memset(&h, 0, sizeof h);
+    h.cls = GC_CUBE;
+    h.target = (int32_t)(j - i);
+    int s = 0;
+    for (int b = 0; b < k; ++b)
+      if (bits >> b & 1u) h.cmask |= (uint64_t)b << (8 * s++);
+    out.push_back(h);
+    out.insert(out.end(), run.begin() + i, run.begin() + j);
+    i = j;
+  }
+}
 
 void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &P) {
   P = Plan();
@@ -348,7 +452,13 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
       P.fused_gates.push_back(g);
       ++ng;
     }
-    d.ngates = ng;
+    if (cfg.cubes && k >= 8 && ng > 0) {
+      const size_t first = P.pass_gate_offset.back();
+      std::vector<DevGate> run(P.fused_gates.begin() + first, P.fused_gates.end());
+      P.fused_gates.resize(first);
+      group_cubes(run, k, P.fused_gates);
+    }
+    d.ngates = (int)(P.fused_gates.size() - P.pass_gate_offset.back());
     P.step_qmask.push_back(d.qmask);
     P.passes.push_back(d);
     P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, ng});

@@ -15,6 +15,7 @@ struct PlanConfig {
   bool fusion = true;       // false: every gate becomes a single-gate sweep
   bool single_as_sweep = true;  // a pass holding one gate is emitted as a sweep instead
   bool init_first = false;  // the first pass starts from |init_x> (batched / served states)
+  bool cubes = false;       // group each pass's gates into register cubes (complex64 passes, k >= 8)
   uint64_t init_x = 0;
 };
 
@@ -54,10 +55,19 @@ void fill_coefficients(DevGate &g, const double *U);
 // Returns SV_OK or an sv_status error with `why` set.
 int validate_gate(const sv_gate &g, int n, std::string &why);
 
+// Split one pass's gates (chunk-local targets, in order) into register cubes: appends to `out` a GC_CUBE
+// header before each run.  Order is kept; every gate lands in exactly one cube.
+void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out);
+
 // Plan `ngates` validated records; perm (logical -> physical) is read and updated by SWAP relabelling.
 void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &out);
 
 // Transpositions (physical bit pairs) that bring `perm` back to the identity, in order; updates perm.
 std::vector<std::pair<int, int>> canonicalize_steps(std::vector<int> &perm);
+
+// The same transpositions as gate-free fused passes whose store permutes bits (the paper's relabelling,
+// Sec. VI.B, done as data movement): consecutive transpositions on disjoint bits share a pass while their
+// bits and the c low bits fit in the chunk.  Updates perm to the identity.
+std::vector<PassDesc> canonicalize_passes(int n, const PlanConfig &cfg, std::vector<int> &perm);
 
 } // namespace svi

@@ -232,7 +232,7 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   uint64_t key = 1469598103934665603ull;
   key = hash_bytes(gates, ngates * sizeof(sv_gate), key);
   key = hash_bytes(s->perm.data(), s->perm.size() * sizeof(int), key);
-  const int opts[6] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical};
+  const int opts[7] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical, f64_share_of(s)};
   key = hash_bytes(opts, sizeof opts, key);
   key = hash_bytes(&s->psi, sizeof s->psi, key);
   auto it = s->graphs.find(key);
@@ -294,14 +294,7 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   int rc = SV_OK;
   if (e == cudaSuccess) {
     rc = run_plan(s, P, ent.d_gates, cap, ent.evs.empty() ? nullptr : ent.evs.data(), true);
-    if (rc == SV_OK && s->canonical) {
-      std::vector<int> pp = perm;
-      for (const auto &ab : canonicalize_steps(pp)) {
-        const cudaError_t e2 = launch_remap_swap(s->psi, s->n, mode_of(s), ab.first, ab.second, cap);
-        if (e2 != cudaSuccess) { rc = cuda_fail(e2, "bit-swap pass"); break; }
-      }
-      perm = pp;
-    }
+    if (rc == SV_OK && s->canonical) rc = canonicalize_on(s, perm, cap, nullptr);
     e = cudaStreamEndCapture(cap, &graph);
   }
   s->renorm_period = saved_period;

@@ -28,6 +28,7 @@ struct sv_state {
   std::vector<int> perm;      // logical qubit -> physical bit
   int chunk_k = 0;            // 0 = default
   int fusion = 1;
+  int cubes = 1;              // complex64: register cubes in fused passes (SV_OPT_CUBES)
   int canonical = 0;
   int f64_share = -1;         // -1 = library default (SV_OPT_F64_SHARE)
   int64_t renorm_period = 0;
@@ -73,6 +74,8 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st,
 int ensure_event_pool(sv_state *s, size_t steps);
 std::vector<int> step_kinds(const Plan &P);
 int canonicalize_now(sv_state *s);
+// Queue the bit-permutation passes that bring `perm` to the identity on stream st (perm is updated).
+int canonicalize_on(sv_state *s, std::vector<int> &perm, cudaStream_t st, int *npasses);
 // Percent of complex128 double-float chunks done in native FP64 alongside (see SV_OPT_F64_SHARE).
 constexpr int kDefaultF64Share = 18;
 int f64_share_of(const sv_state *s);

@@ -212,6 +212,98 @@ def test_buffer_state_over_torch_tensor_stays_in_logical_order():
         B.sv_destroy(h)
 
 
+@pytest.mark.parametrize("n,chunk_k", [(8, 8), (13, 0), (17, 0), (17, 9), (20, 12)])
+def test_c64_register_cubes_identical_to_per_gate_passes(n, chunk_k):
+    """Complex64 passes apply runs of gates on at most four chunk bits from registers (SV_OPT_CUBES).  The
+    same arithmetic in the same order as the per-gate shared-memory loop: results are bit-identical, and
+    within the complex64 tolerance of the oracle.  Circuits mix every gate class, in-cube and out-of-cube
+    controls, and diagonal gates on bits outside the cube and outside the chunk."""
+    rng = np.random.default_rng(700 + n)
+    gates = []
+    for layer in range(6):
+        for q in range(n):
+            r = rng.integers(0, 6)
+            if r == 0:
+                gates.append(C.gate_u(C.haar_u2(rng), q))
+            elif r == 1:
+                gates.append(C.gate_u(np.diag(np.exp(1j * rng.uniform(0, 6.3, 2))), q, [int((q + 3) % n)]))
+            elif r == 2:
+                gates.append(C.gate_u(C.phase(rng.uniform(0, 6.3)), q, [int((q + n // 2) % n)]))
+            elif r == 3:
+                gates.append(C.cnot(int(rng.integers(0, n - 1) + q + 1) % n, q))
+            elif r == 4:
+                ph = np.exp(1j * rng.uniform(0, 6.3, 2))
+                gates.append(C.gate_u(np.array([[0, ph[0]], [ph[1], 0]]), q))
+            else:
+                gates.append(C.gate_u(C.haar_u2(rng), q, [int((q + 1) % n), int((q + 5) % n)]))
+    w = C.pack(gates)
+    psi0 = C.random_state(n, seed=n + 1)
+    outs = []
+    for cubes in (0, 1):
+        h = make_state(n, B.SV_C64, B.SV_ARITH_AUTO, psi0=psi0, chunk_k=chunk_k)
+        try:
+            B.sv_set_option(h, B.SV_OPT_CUBES, cubes)
+            B.sv_apply_circuit(h, w)
+            outs.append(B.sv_read_amplitudes(h))
+        finally:
+            B.sv_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+    want = run_oracle(n, w, psi0.astype(np.complex64).astype(np.complex128))
+    assert_close(outs[1].astype(np.complex128), want, B.SV_C64, "register cubes")
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n,chunk_k", [(2, 0), (5, 0), (13, 0), (16, 0), (21, 0), (21, 6), (22, 9)])
+def test_canonicalize_random_layouts_is_bit_exact(mode, n, chunk_k):
+    """SWAPs only relabel qubits (Sec. VI.B); sv_canonicalize then moves the data back into logical order with
+    bit-permutation passes.  Pure data movement: the result equals the oracle's exactly, in every mode, for
+    random layouts that mix the low (row) bits with high ones and need several passes."""
+    _, dtype, arith = mode
+    rng = np.random.default_rng(100 + n + chunk_k)
+    psi0 = C.random_state(n, seed=n)
+    if dtype == B.SV_C64:
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    swaps = C.pack([C.gate_swap(*rng.choice(n, 2, replace=False)) for _ in range(3 * n)]) if n > 1 else C.pack([])
+    want = run_oracle(n, swaps, psi0)
+    h = make_state(n, dtype, arith, psi0=psi0, chunk_k=chunk_k)
+    try:
+        B.sv_apply_circuit(h, swaps)
+        layout = list(B.sv_get_layout(h))
+        assert np.array_equal(B.sv_read_amplitudes(h).astype(np.complex128), want)
+        B.sv_canonicalize(h)
+        assert list(B.sv_get_layout(h)) == list(range(n))
+        got = B.sv_read_amplitudes(h).astype(np.complex128)
+        assert np.array_equal(got, want), f"layout was {layout}"
+    finally:
+        B.sv_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [B.SV_C128, B.SV_C64], ids=["c128", "c64"])
+def test_buffer_state_graph_replay_stays_in_logical_order(dtype):
+    """A buffer state (caller-owned memory, always in logical order) through the captured-graph path: the
+    graph ends with the bit-permutation passes that undo the QFT's SWAP relabelling."""
+    torch = pytest.importorskip("torch")
+    n = 18
+    psi0 = C.random_state(n, seed=19)
+    tdt = torch.complex64 if dtype == B.SV_C64 else torch.complex128
+    t = torch.from_numpy(psi0).to(tdt).to("cuda")
+    torch.cuda.synchronize()
+    start = t.clone()
+    w = C.pack(C.qft(n))
+    want = run_oracle(n, w, t.cpu().numpy().astype(np.complex128))
+    h = B.sv_create_from_buffer(n, dtype, t.data_ptr())
+    try:
+        for rep in range(2):
+            t.copy_(start)
+            torch.cuda.synchronize()
+            B.sv_apply_circuit_graph(h, w)
+            B.sv_sync(h)
+            assert list(B.sv_get_layout(h)) == list(range(n))
+            assert_close(t.cpu().numpy().astype(np.complex128), want, dtype, f"graph replay {rep}")
+    finally:
+        B.sv_destroy(h)
+
+
 def test_host_validation_leaves_state_untouched():
     n = 6
     h = make_state(n, B.SV_C128, B.SV_ARITH_DF32, x0=5)
