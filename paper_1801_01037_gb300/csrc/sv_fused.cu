@@ -75,23 +75,24 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
 // the two paths give identical results.  cs: the gate's control bits inside the cube, as cube bits.
 using C64 = Arith<MODE_C64_F32>;
 
-template <int J, int CLS>
+template <int J, int CLS, bool CTL>
 __device__ __forceinline__ void cube_pairs(float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     if (s & (1 << J)) continue;
-    if (((uint32_t)s & cs) != cs) continue;
+    if (CTL && ((uint32_t)s & cs) != cs) continue;
     apply_pair<MODE_C64_F32>(CLS, cf, v[s], v[s | (1 << J)]);
   }
 }
 
-template <int CLS>
+// CTL = false: the gate has no control bit inside the cube (cs = 0), so no per-pair test is compiled.
+template <int CLS, bool CTL = true>
 __device__ __forceinline__ void cube_pairs_at(int j, float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
   switch (j) {
-    case 0: cube_pairs<0, CLS>(v, cf, cs); break;
-    case 1: cube_pairs<1, CLS>(v, cf, cs); break;
-    case 2: cube_pairs<2, CLS>(v, cf, cs); break;
-    default: cube_pairs<3, CLS>(v, cf, cs); break;
+    case 0: cube_pairs<0, CLS, CTL>(v, cf, cs); break;
+    case 1: cube_pairs<1, CLS, CTL>(v, cf, cs); break;
+    case 2: cube_pairs<2, CLS, CTL>(v, cf, cs); break;
+    default: cube_pairs<3, CLS, CTL>(v, cf, cs); break;
   }
 }
 
@@ -134,9 +135,17 @@ __device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint32_t po
       const int t = g.target;
       const int j = t == p0 ? 0 : t == p1 ? 1 : t == p2 ? 2 : t == p3 ? 3 : -1;
       CoefF32 cf;
-      if (cls != GC_X) C64::coef(cf, g);
+      if (cls != GC_X) {
+        // The complex64 coefficients: two 16-byte loads (DevGate records are 192 bytes, 16-byte aligned).
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(g.qh)), b = __ldg(reinterpret_cast<const float4 *>(g.qh) + 1);
+        cf.q[0] = a.x; cf.q[1] = a.y; cf.q[2] = a.z; cf.q[3] = a.w;
+        cf.q[4] = b.x; cf.q[5] = b.y; cf.q[6] = b.z; cf.q[7] = b.w;
+      }
       switch (cls) {
-        case GC_GENERAL: cube_pairs_at<GC_GENERAL>(j, v, cf, cs); break;
+        case GC_GENERAL:
+          if (cs == 0) cube_pairs_at<GC_GENERAL, false>(j, v, cf, cs);
+          else cube_pairs_at<GC_GENERAL>(j, v, cf, cs);
+          break;
         case GC_ANTIDIAG: cube_pairs_at<GC_ANTIDIAG>(j, v, cf, cs); break;
         case GC_X: cube_pairs_at<GC_X>(j, v, cf, cs); break;
         default:
