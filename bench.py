@@ -258,7 +258,7 @@ def run_ours(args):
 
     # Chunk size per dtype from the autotuner, timed on a 4-layer circuit of the same shape (untimed here).
     chunk_k, tuning = {}, {}
-    f64_share = 18  # the library's default share of chunks done on the FP64 pipe
+    f64_share = B.SV_F64_SHARE_DEFAULT  # share of chunks done on the FP64 pipe unless the autotuner picks one
     if not args.no_autotune:
         from paper_1801_01037_gb300 import autotune
         probe = C.random_workload(args.n, 4, seed=SEED + 7).gates
@@ -428,9 +428,10 @@ def run_ours(args):
         "sweep_roofline": sweeps,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "gates/s",
-                "h2d_bytes_per_step": st["fused_gates"] * 224,
+                "h2d_bytes_per_step": (st["fused_gates"] + st["sweep_gates"]) * 192,
                 "d2h_bytes_per_step": 8 + READ_COUNT * 16,
-                "note": "h2d: planned gate records (208 B) plus group descriptors (16 B), upper bound per gate"},
+                "note": "h2d: the planned 192-byte device gate records, uploaded per step (a single-gate sweep "
+                        "takes its record as a kernel parameter); d2h: the FP64 norm and 1024 amplitudes"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": c128["clocks"],
         "norm_last_step": c128["norm"],

@@ -80,9 +80,11 @@ typedef struct sv_server sv_server;
                                    (also inside captured graphs); read them with sv_profile_last */
 #define SV_OPT_F64_SHARE 7      /* complex128 with SV_ARITH_DF32: percent (0..99) of each fused pass's chunks
                                    computed with native FP64 by one CTA per SM, in parallel with the
-                                   double-float CTAs (the FP64 pipe is otherwise idle); -1 = default (15).
+                                   double-float CTAs (the FP64 pipe is otherwise idle); -1 = default
+                                   (SV_F64_SHARE_DEFAULT).
                                    Which chunks use FP64 depends only on their index: results are
                                    reproducible run to run. */
+#define SV_F64_SHARE_DEFAULT 15
 #define SV_OPT_CUBES 8          /* complex64: 1 = apply runs of gates on at most 4 chunk bits from registers
                                    (one shared-memory round trip per run), the default; 0 = one
                                    shared-memory round trip per gate.  Results are identical either way. */

@@ -77,7 +77,7 @@ int canonicalize_now(sv_state *s);
 // Queue the bit-permutation passes that bring `perm` to the identity on stream st (perm is updated).
 int canonicalize_on(sv_state *s, std::vector<int> &perm, cudaStream_t st, int *npasses);
 // Percent of complex128 double-float chunks done in native FP64 alongside (see SV_OPT_F64_SHARE).
-constexpr int kDefaultF64Share = 15;
+constexpr int kDefaultF64Share = SV_F64_SHARE_DEFAULT;
 int f64_share_of(const sv_state *s);
 int maybe_renormalize(sv_state *s, int applied);
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero);

@@ -36,6 +36,20 @@ def test_every_declared_entry_point_is_exported(lib):
     assert sorted(B.EXPORTED) == names
 
 
+def test_binding_constants_match_header():
+    """Every integer #define of include/sv.h that the Python binding also names has the same value there."""
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SV_\w+)\s+(-?\d+)\b", src, re.M))
+    shared = [k for k in defs if hasattr(B, k)]
+    assert len(shared) >= 10
+    for k in shared:
+        assert getattr(B, k) == int(defs[k]), k
+    enums = dict(re.findall(r"\b(SV_\w+)\s*=\s*(-?\d+)", src))
+    for k, v in enums.items():
+        if hasattr(B, k):
+            assert getattr(B, k) == int(v), k
+
+
 def test_gate_record_matches_header(lib):
     src = open(os.path.join(ROOT, "include", "sv.h")).read()
     assert "double U[8];" in src and C.GATE_DTYPE.itemsize == 96
