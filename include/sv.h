@@ -85,6 +85,9 @@ typedef struct sv_server sv_server;
                                    Which chunks use FP64 depends only on their index: results are
                                    reproducible run to run. */
 #define SV_F64_SHARE_DEFAULT 15
+#define SV_OPT_PRODUCT_START 9  /* 1 = fold leading single-qubit gates into the factors while the state is a
+                                   product state (sv_init_product), the default; 0 = never (every gate runs
+                                   as a kernel, e.g. to time single-gate sweeps on a fresh state) */
 #define SV_OPT_CUBES 8          /* complex64: 1 = apply runs of gates on at most 4 chunk bits from registers
                                    (one shared-memory round trip per run), the default; 0 = one
                                    shared-memory round trip per gate.  Results are identical either way. */
@@ -107,8 +110,25 @@ sv_status sv_create_from_buffer(int n, sv_dtype dtype, void *dev_ptr, void *stre
 /* Release the handle and, for sv_create states, the device memory.  NULL is accepted. */
 sv_status sv_destroy(sv_state *s);
 
-/* |x>: amplitude x = 1, all others 0.  x < 2^n.  Resets the layout to the identity. */
+/* |x>: amplitude x = 1, all others 0.  x < 2^n.  Resets the layout to the identity.  Like sv_create's
+ * |0...0>, the result is a product state (see sv_init_product). */
 sv_status sv_init_basis(sv_state *s, uint64_t x);
+
+/* Product state |psi_0 ... psi_{n-1}> (Sec. V, the per-qubit form of a state with no entanglement): qubit t
+ * in alpha_t|0> + beta_t|1>, so amplitude k = prod_t (bit t of k ? beta_t : alpha_t).  factors: 4n doubles
+ * in host memory, (re alpha_t, im alpha_t, re beta_t, im beta_t) for t = 0..n-1; each |alpha_t|^2 +
+ * |beta_t|^2 must be 1 within 1e-10.  The amplitudes are formed on the GPU in FP64 (two tables of partial
+ * products, one complex product per amplitude; complex64 states round the result).  Resets the layout.
+ *
+ * While a state is still a product state (since sv_create, sv_init_basis or sv_init_product, no gate has
+ * entangled it), the apply calls fold every uncontrolled single-qubit gate (and SWAP) that acts on qubits no
+ * earlier remaining gate of the call touches into those qubits' factors on the host (2x2 products in FP64),
+ * as the paper suggests for the gates at the start of a circuit, re-form the amplitudes once, and plan only
+ * the rest.  Re-forming writes the whole state, so the fold is taken only when nothing else remains or at
+ * least max(2, n/4) gates fold (option SV_OPT_PRODUCT_START turns it off).  sv_last_plan_stats reports the
+ * folded gates.
+ * Errors: SV_ERR_ARG (NULL, non-finite or non-normalised factor), SV_ERR_CUDA. */
+sv_status sv_init_product(sv_state *s, const double *factors);
 
 /* Copy `count` amplitudes from host memory (state's dtype, logical order) into indices first..first+count-1
  * (checkpoint restore). */
@@ -216,10 +236,10 @@ sv_status sv_sync(sv_state *s);
 
 /* Planner statistics of the last apply call: passes launched, gates applied inside fused passes, gates
  * applied by single-gate sweeps, SWAPs folded into the layout, bit-swap passes of the apply call (buffer
- * states) plus the bit-permutation passes of canonicalisations since the state was created.  Any pointer may
- * be NULL. */
+ * states) plus the bit-permutation passes of canonicalisations since the state was created, and gates
+ * folded into the factors of a product state (sv_init_product).  Any pointer may be NULL. */
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
-                             int *remaps);
+                             int *remaps, int *absorbed);
 
 /* With SV_OPT_PROFILE on: device time of the launches of the most recent apply call (or graph replay) of one
  * kind (0 = fused chunk pass, 1 = single-gate sweep, 2 = bit-swap pass), summed over its launches.  Waits for

@@ -78,6 +78,17 @@ def basis_state(n: int, x: int = 0) -> np.ndarray:
     return psi
 
 
+def product_state(factors) -> np.ndarray:
+    """The product state of Sec. V, |psi_0 ... psi_{n-1}>, with qubit t in alpha_t|0> + beta_t|1>
+    (factors[t] = (alpha_t, beta_t)): the Kronecker product of the one-qubit vectors, qubit 0 on the
+    least significant index bit (stride 2^t, Sec. V.A), so amplitude k = prod_t (bit t of k ? beta_t : alpha_t)."""
+    f = np.asarray(factors, dtype=np.complex128).reshape(-1, 2)
+    psi = np.ones(1, dtype=np.complex128)
+    for t in range(f.shape[0]):
+        psi = np.kron(f[t], psi)  # qubit t becomes the most significant bit so far
+    return psi
+
+
 def apply_gate(psi: np.ndarray, u, target: int, controls=()) -> np.ndarray:
     """Apply a (controlled) 2x2 unitary in place; returns ``psi``."""
     n = _nqubits(psi)

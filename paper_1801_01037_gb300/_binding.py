@@ -40,12 +40,13 @@ SV_OPT_PROFILE = 6
 SV_OPT_F64_SHARE = 7
 SV_OPT_CUBES = 8
 SV_F64_SHARE_DEFAULT = 15
+SV_OPT_PRODUCT_START = 9
 
 SV_GATE_U = 0
 SV_GATE_SWAP = 1
 
 EXPORTED = [
-    "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_write_amplitudes", "sv_set_option",
+    "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_init_product", "sv_write_amplitudes", "sv_set_option",
     "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_swap", "sv_apply_circuit",
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_server_create", "sv_server_destroy",
@@ -79,6 +80,7 @@ def load(path: str | None = None):
         "sv_create_from_buffer": [i, i, P, P, PP],
         "sv_destroy": [P],
         "sv_init_basis": [P, u64],
+        "sv_init_product": [P, P],
         "sv_write_amplitudes": [P, u64, u64, P],
         "sv_set_option": [P, i, ctypes.c_int64],
         "sv_get_info": [P, P, P, P],
@@ -97,7 +99,7 @@ def load(path: str | None = None):
         "sv_norm_noalloc": [P, i, i, P, P],
         "sv_renormalize": [P],
         "sv_sync": [P],
-        "sv_last_plan_stats": [P, P, P, P, P, P],
+        "sv_last_plan_stats": [P, P, P, P, P, P, P],
         "sv_plan_dry_run": [i, i, i, P, sz, P, P, P, P, i, P],
         "sv_profile_last": [P, i, ctypes.POINTER(i), ctypes.POINTER(d)],
         "sv_run_batch": [i, P, i, P, P, P, P],
@@ -157,6 +159,12 @@ def sv_destroy(h: int) -> None:
 
 def sv_init_basis(h: int, x: int) -> None:
     _check(load().sv_init_basis(h, x))
+
+
+def sv_init_product(h: int, factors) -> None:
+    """Product state: factors[t] = (alpha_t, beta_t), complex, qubit t in alpha_t|0> + beta_t|1>."""
+    f = np.ascontiguousarray(np.asarray(factors, dtype=np.complex128).reshape(-1, 2)).view(np.float64).ravel()
+    _check(load().sv_init_product(h, f.ctypes.data))
 
 
 def sv_write_amplitudes(h: int, first: int, values: np.ndarray) -> None:
@@ -275,9 +283,9 @@ def sv_sync(h: int) -> None:
 
 
 def sv_last_plan_stats(h: int) -> dict:
-    v = [ctypes.c_int() for _ in range(5)]
+    v = [ctypes.c_int() for _ in range(6)]
     _check(load().sv_last_plan_stats(h, *[ctypes.byref(x) for x in v]))
-    return dict(zip(["passes", "fused_gates", "sweep_gates", "relabels", "remaps"], [x.value for x in v]))
+    return dict(zip(["passes", "fused_gates", "sweep_gates", "relabels", "remaps", "absorbed"], [x.value for x in v]))
 
 
 def sv_profile_last(h: int, kind: int = 0):

@@ -1,5 +1,6 @@
 // C ABI: handles, host-side validation, planning and launch of the kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -189,6 +190,117 @@ int canonicalize_now(sv_state *s) {
   return rc;
 }
 
+// ---- Product states (Sec. V: a state without entanglement is the Kronecker product of one-qubit states) ----
+
+void set_basis_product(sv_state *s, uint64_t x) {
+  s->pf.assign(4 * (size_t)s->n, 0.0);
+  s->pm.assign(8 * (size_t)s->n, 0.0);
+  for (int t = 0; t < s->n; ++t) {
+    s->pf[4 * t + ((x >> t) & 1ull ? 2 : 0)] = 1.0;
+    s->pm[8 * t + 0] = 1.0;  // M_t = identity
+    s->pm[8 * t + 6] = 1.0;
+  }
+  s->product = true;
+}
+
+// Form psi = (x)_t M_t f_t on the GPU (every amplitude is written).
+int expand_product(sv_state *s) {
+  const size_t head = 12 * (size_t)s->n * sizeof(double);
+  const size_t need = head + product_table_entries(s->n) * 2 * sizeof(double);
+  cudaError_t e;
+  if (s->d_prod_cap < need) {
+    if (s->d_prod) {
+      if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "stream sync");
+      cudaFree(s->d_prod);
+      s->d_prod = nullptr;
+      s->d_prod_cap = 0;
+    }
+    if ((e = cudaMalloc(&s->d_prod, need)) != cudaSuccess) return set_error(SV_ERR_OOM, "product-state scratch allocation failed");
+    s->d_prod_cap = need;
+  }
+  std::vector<double> fm(12 * (size_t)s->n);
+  for (int t = 0; t < s->n; ++t) {
+    std::memcpy(&fm[12 * t], &s->pf[4 * t], 4 * sizeof(double));
+    std::memcpy(&fm[12 * t + 4], &s->pm[8 * t], 8 * sizeof(double));
+  }
+  // Pageable source: the call returns once the bytes are staged, so `fm` may go out of scope.
+  if ((e = cudaMemcpyAsync(s->d_prod, fm.data(), head, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+    return cuda_fail(e, "product factors upload");
+  for (int t = 0; t < s->n; ++t) s->perm[t] = t;
+  e = launch_init_product(s->psi, s->n, mode_of(s), (const double *)s->d_prod, (char *)s->d_prod + head, s->stream);
+  return e == cudaSuccess ? SV_OK : cuda_fail(e, "product state");
+}
+
+// While the state is a product state, move every single-qubit gate (and SWAP) that acts only on qubits no
+// earlier remaining gate touches to the front and fold it into the qubits' factors: M_t <- U M_t (FP64), SWAP
+// exchanges two qubits' factors.  Gates on disjoint qubits commute, so the order of the rest is kept and the
+// result is unchanged.  `rest` receives the remaining records in order; returns the number folded.
+int absorb_leading(int n, const sv_gate *gates, size_t ngates, std::vector<double> &pf, std::vector<double> &pm,
+                   std::vector<sv_gate> &rest) {
+  std::vector<char> touched(n, 0);
+  int folded = 0;
+  rest.clear();
+  for (size_t i = 0; i < ngates; ++i) {
+    const sv_gate &g = gates[i];
+    if (g.kind == SV_GATE_U && g.ncontrols == 0 && !touched[g.target]) {
+      double *m = &pm[8 * (size_t)g.target];
+      double r[8];
+      for (int row = 0; row < 2; ++row)
+        for (int col = 0; col < 2; ++col) {
+          double re = 0.0, im = 0.0;
+          for (int j = 0; j < 2; ++j) {
+            const double ur = g.U[4 * row + 2 * j], ui = g.U[4 * row + 2 * j + 1];
+            const double mr = m[4 * j + 2 * col], mi = m[4 * j + 2 * col + 1];
+            re += ur * mr - ui * mi;
+            im += ur * mi + ui * mr;
+          }
+          r[4 * row + 2 * col] = re;
+          r[4 * row + 2 * col + 1] = im;
+        }
+      std::memcpy(m, r, sizeof r);
+      ++folded;
+      continue;
+    }
+    if (g.kind == SV_GATE_SWAP && !touched[g.target] && !touched[g.target2]) {
+      for (int j = 0; j < 4; ++j) std::swap(pf[4 * (size_t)g.target + j], pf[4 * (size_t)g.target2 + j]);
+      for (int j = 0; j < 8; ++j) std::swap(pm[8 * (size_t)g.target + j], pm[8 * (size_t)g.target2 + j]);
+      ++folded;
+      continue;
+    }
+    touched[g.target] = 1;
+    if (g.kind == SV_GATE_SWAP) touched[g.target2] = 1;
+    for (int c = 0; c < g.ncontrols; ++c) touched[g.controls[c]] = 1;
+    rest.push_back(g);
+  }
+  return folded;
+}
+
+// Apply-call prologue for product states: fold what can be folded, re-form the amplitudes, and point
+// (gates, ngates) at the remaining records (kept in `rest`).  Re-forming costs one write of the state, so
+// the fold is taken when it leaves nothing else to run or folds at least max(2, n/4) gates (a gate inside a
+// fused pass costs a fraction of a pass).  The state stays a product state only if nothing remains.
+int product_prologue(sv_state *s, const sv_gate *&gates, size_t &ngates, std::vector<sv_gate> &rest) {
+  s->st_absorbed = 0;
+  if (!s->product || ngates == 0) return SV_OK;
+  if (!s->product_start) {
+    s->product = false;
+    return SV_OK;
+  }
+  std::vector<double> pf = s->pf, pm = s->pm;
+  const int folded = absorb_leading(s->n, gates, ngates, pf, pm, rest);
+  if (folded > 0 && (rest.empty() || folded >= std::max(2, s->n / 4))) {
+    s->pf.swap(pf);
+    s->pm.swap(pm);
+    const int rc = expand_product(s);
+    if (rc != SV_OK) return rc;
+    s->st_absorbed = folded;
+    gates = rest.data();
+    ngates = rest.size();
+  }
+  if (ngates > 0) s->product = false;
+  return SV_OK;
+}
+
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero) {
   const size_t bytes = amp_bytes(dt) << n;
   // Host-side failure injection for tests: with SV_FAULT_ALLOC set, every state allocation fails as if
@@ -223,6 +335,7 @@ int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_z
       sv_destroy(s);
       return cuda_fail(e, "init");
     }
+    set_basis_product(s, 0);
   }
   *out = s;
   return SV_OK;
@@ -289,6 +402,7 @@ sv_status sv_destroy(sv_state *s) {
   if (s->d_scalars) cudaFree(s->d_scalars);
   if (s->d_sched) cudaFree(s->d_sched);
   if (s->d_read) cudaFree(s->d_read);
+  if (s->d_prod) cudaFree(s->d_prod);
   if (s->stage_ev) cudaEventDestroy(s->stage_ev);
   for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
   for (auto &kv : s->graphs)
@@ -303,7 +417,28 @@ sv_status sv_init_basis(sv_state *s, uint64_t x) {
   for (int t = 0; t < s->n; ++t) s->perm[t] = t;
   s->gates_since_renorm = 0;
   cudaError_t e = launch_init_basis(s->psi, s->n, mode_of(s), x, s->stream);
-  return e == cudaSuccess ? SV_OK : cuda_fail(e, "init");
+  if (e != cudaSuccess) return cuda_fail(e, "init");
+  set_basis_product(s, x);
+  return SV_OK;
+}
+
+sv_status sv_init_product(sv_state *s, const double *factors) {
+  if (!s || !factors) return set_error(SV_ERR_ARG, "NULL argument");
+  for (int t = 0; t < s->n; ++t) {
+    const double *f = factors + 4 * t;
+    double nrm = 0.0;
+    for (int j = 0; j < 4; ++j) {
+      if (!std::isfinite(f[j])) return set_error(SV_ERR_ARG, "factor " + std::to_string(t) + " is not finite");
+      nrm += f[j] * f[j];
+    }
+    if (std::fabs(nrm - 1.0) > 1e-10) return set_error(SV_ERR_ARG, "factor " + std::to_string(t) + " is not normalised");
+  }
+  set_basis_product(s, 0);
+  std::memcpy(s->pf.data(), factors, 4 * (size_t)s->n * sizeof(double));
+  s->gates_since_renorm = 0;
+  const int rc = expand_product(s);
+  if (rc != SV_OK) s->product = false;
+  return rc;
 }
 
 sv_status sv_set_option(sv_state *s, int option, int64_t value) {
@@ -320,6 +455,7 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
     case SV_OPT_CUBES: s->cubes = value ? 1 : 0; return SV_OK;
+    case SV_OPT_PRODUCT_START: s->product_start = value ? 1 : 0; return SV_OK;
     case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
     case SV_OPT_F64_SHARE:
       if (value < -1 || value > 99) return set_error(SV_ERR_ARG, "FP64 share must be -1 (default) or 0..99 percent");
@@ -362,6 +498,9 @@ static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool 
     const int rc = validate_gate(gates[i], s->n, why);
     if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
   }
+  std::vector<sv_gate> rest;
+  const int prc = product_prologue(s, gates, ngates, rest);
+  if (prc != SV_OK) return prc;
   PlanConfig cfg = plan_config(s);
   if (single) cfg.fusion = false;
   Plan P;
@@ -473,8 +612,10 @@ sv_status sv_sync(sv_state *s) {
   return e == cudaSuccess ? SV_OK : cuda_fail(e, "stream sync");
 }
 
-sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels, int *remaps) {
+sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels, int *remaps,
+                             int *absorbed) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  if (absorbed) *absorbed = s->st_absorbed;
   if (passes) *passes = s->st_passes;
   if (fused_gates) *fused_gates = s->st_fused;
   if (sweep_gates) *sweep_gates = s->st_sweeps;

@@ -72,6 +72,10 @@ static_assert(sizeof(PassDesc) == 104, "PassDesc layout");
 // Kernel launchers (sv_kernels.cu).  All return cudaGetLastError() of the launch.
 // ---------------------------------------------------------------------------------------------------------
 cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream_t st);
+// Product state from d_fm (12 doubles per qubit: f_t then M_t), using d_tab as scratch for
+// product_table_entries(n) double2 values.
+uint64_t product_table_entries(int n);
+cudaError_t launch_init_product(void *psi, int n, int mode, const double *d_fm, void *d_tab, cudaStream_t st);
 
 // Scratch of the mixed FP64 / double-float pass: one election slot per SM and one chunk counter per role.
 constexpr int kSchedSlots = 256;

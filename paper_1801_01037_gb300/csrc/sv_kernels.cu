@@ -346,6 +346,59 @@ cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream
   return cudaGetLastError();
 }
 
+// Product state (Sec. V): amplitude k = prod_t g_t[bit t of k] with g_t = M_t f_t.  Table entry i < 2^h
+// holds the product over qubits 0..h-1 for low index bits i, entry 2^h + j the product over qubits h..n-1 for
+// high index bits j (FP64, qubits in ascending order).
+__global__ void k_product_tables(const double *__restrict__ fm, int n, int h, double2 *__restrict__ tab) {
+  const uint64_t nlo = 1ull << h, total = nlo + (1ull << (n - h));
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    const bool lo = i < nlo;
+    const uint64_t x = lo ? i : i - nlo;
+    const int t0 = lo ? 0 : h, t1 = lo ? h : n;
+    double re = 1.0, im = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      const double *f = fm + 12 * t;
+      const double *r = f + 4 + 4 * (int)((x >> (t - t0)) & 1ull);  // row b of M_t
+      const double gr = r[0] * f[0] - r[1] * f[1] + r[2] * f[2] - r[3] * f[3];
+      const double gi = r[0] * f[1] + r[1] * f[0] + r[2] * f[3] + r[3] * f[2];
+      const double nr = re * gr - im * gi, ni = re * gi + im * gr;
+      re = nr;
+      im = ni;
+    }
+    tab[i] = make_double2(re, im);
+  }
+}
+
+template <typename G>
+__global__ void k_init_product(G *__restrict__ psi, int n, int h, const double2 *__restrict__ tab) {
+  const uint64_t N = 1ull << n, mlo = (1ull << h) - 1ull;
+  const double2 *hi = tab + (1ull << h);
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < N; k += (uint64_t)gridDim.x * blockDim.x) {
+    const double2 a = tab[k & mlo], b = hi[k >> h];
+    if constexpr (sizeof(G) == 16) {
+      psi[k] = G{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+    } else {
+      // complex64: the tables rounded to float, one FP32 complex product (relative error a few 2^-24)
+      const float ar = (float)a.x, ai = (float)a.y, br = (float)b.x, bi = (float)b.y;
+      psi[k] = G{ar * br - ai * bi, ar * bi + ai * br};
+    }
+  }
+}
+
+uint64_t product_table_entries(int n) { return (1ull << (n / 2)) + (1ull << (n - n / 2)); }
+
+cudaError_t launch_init_product(void *psi, int n, int mode, const double *d_fm, void *d_tab, cudaStream_t st) {
+  const int h = n / 2;
+  const uint64_t entries = product_table_entries(n);
+  k_product_tables<<<grid_for(entries, 256), 256, 0, st>>>(d_fm, n, h, (double2 *)d_tab);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned grid = grid_for(1ull << n, 256);
+  if (mode == MODE_C64_F32) k_init_product<float2><<<grid, 256, 0, st>>>((float2 *)psi, n, h, (const double2 *)d_tab);
+  else k_init_product<double2><<<grid, 256, 0, st>>>((double2 *)psi, n, h, (const double2 *)d_tab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st) {
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const uint64_t items = 1ull << (n - 2);

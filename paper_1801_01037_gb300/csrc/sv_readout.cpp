@@ -131,6 +131,7 @@ sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const
   int rc = check_range(s, first, count);
   if (rc != SV_OK) return rc;
   if (!identity_layout(s) && (rc = canonicalize_now(s)) != SV_OK) return rc;
+  s->product = false;
   const size_t ab = amp_bytes(s->dtype);
   cudaError_t e = cudaMemcpyAsync((char *)s->psi + first * ab, host_in, count * ab, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -214,6 +215,7 @@ sv_status sv_sample(sv_state *s, const double *u, uint64_t count, uint64_t *out)
 
 sv_status sv_renormalize(sv_state *s) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  s->product = false;
   double *d_out = s->d_scalars + norm_parts();
   cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
   if (e == cudaSuccess) e = launch_scale(s->psi, s->n, mode_of(s), d_out, s->stream);
@@ -228,11 +230,20 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
     const int rc = validate_gate(gates[i], s->n, why);
     if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
   }
+  std::vector<sv_gate> rest;
+  const int prc = product_prologue(s, gates, ngates, rest);
+  if (prc != SV_OK) return prc;
+  if (ngates == 0 && s->st_absorbed > 0) {  // everything folded into a product state: nothing to capture
+    s->st_passes = s->st_fused = s->st_sweeps = s->st_relabels = s->st_remaps = 0;
+    s->last_evs = nullptr;
+    s->last_kind.clear();
+    return SV_OK;
+  }
   const PlanConfig cfg = plan_config(s);
   uint64_t key = 1469598103934665603ull;
   key = hash_bytes(gates, ngates * sizeof(sv_gate), key);
   key = hash_bytes(s->perm.data(), s->perm.size() * sizeof(int), key);
-  const int opts[7] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical, f64_share_of(s)};
+  const int opts[8] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical, f64_share_of(s), (int)cfg.cubes};
   key = hash_bytes(opts, sizeof opts, key);
   key = hash_bytes(&s->psi, sizeof s->psi, key);
   auto it = s->graphs.find(key);

@@ -46,8 +46,15 @@ struct sv_state {
   // read-out staging (device)
   void *d_read = nullptr;
   size_t d_read_cap = 0;
+  // Product state (sv_init_product): while `product` holds, psi = (x)_t M_t f_t with f_t = pf[4t..4t+3]
+  // (alpha_t, beta_t as re, im) and M_t = pm[8t..8t+7] (row-major re, im), the qubit's folded gates.
+  bool product = false;
+  int product_start = 1;      // SV_OPT_PRODUCT_START
+  std::vector<double> pf, pm;
+  void *d_prod = nullptr;     // device: 12 n doubles (f_t, M_t) then the two partial-product tables
+  size_t d_prod_cap = 0;      // bytes
   // stats of the last apply
-  int st_passes = 0, st_fused = 0, st_sweeps = 0, st_relabels = 0, st_remaps = 0;
+  int st_passes = 0, st_fused = 0, st_sweeps = 0, st_relabels = 0, st_remaps = 0, st_absorbed = 0;
   std::unordered_map<uint64_t, GraphEntry> graphs;
   // profiling (SV_OPT_PROFILE)
   int profile = 0;
@@ -74,6 +81,9 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st,
 int ensure_event_pool(sv_state *s, size_t steps);
 std::vector<int> step_kinds(const Plan &P);
 int canonicalize_now(sv_state *s);
+// Product-state start: fold leading single-qubit gates into the factors and re-form psi; (gates, ngates)
+// then name the remaining records, stored in `rest`.
+int product_prologue(sv_state *s, const sv_gate *&gates, size_t &ngates, std::vector<sv_gate> &rest);
 // Queue the bit-permutation passes that bring `perm` to the identity on stream st (perm is updated).
 int canonicalize_on(sv_state *s, std::vector<int> &perm, cudaStream_t st, int *npasses);
 // Percent of complex128 double-float chunks done in native FP64 alongside (see SV_OPT_F64_SHARE).

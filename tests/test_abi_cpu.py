@@ -44,7 +44,7 @@ def test_binding_constants_match_header():
     assert len(shared) >= 10
     for k in shared:
         assert getattr(B, k) == int(defs[k]), k
-    enums = dict(re.findall(r"\b(SV_\w+)\s*=\s*(-?\d+)", src))
+    enums = dict(re.findall(r"\b(SV_\w+)\s*=\s*(-?\d+)\s*[,}]", src))
     for k, v in enums.items():
         if hasattr(B, k):
             assert getattr(B, k) == int(v), k
@@ -64,6 +64,8 @@ def test_null_and_range_errors_without_device(lib):
     assert lib.sv_create(37, B.SV_C128, None, ctypes.byref(out)) == B.SV_ERR_ARG
     assert lib.sv_create(4, 7, None, ctypes.byref(out)) == B.SV_ERR_ARG
     assert lib.sv_norm(None, None) == B.SV_ERR_ARG
+    assert lib.sv_init_product(None, None) == B.SV_ERR_ARG
+    assert lib.sv_last_plan_stats(None, None, None, None, None, None, None) == B.SV_ERR_ARG
     assert lib.sv_poll(None, 1, None, None) == B.SV_ERR_ARG
     assert b"NULL" in lib.sv_last_error()
 

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import circuits as C
+import oracle
 from test_oracle_pins import dense_gate, dense_swap
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "sv_oracle.c")
@@ -82,3 +83,45 @@ def test_unmutated_copy_passes(tmp_path):
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(tmp_path, name):
     assert pins_detect(build_mutant(tmp_path, name))
+
+
+# ---- product_state (numpy): plausible slips in the Kronecker order or the factor layout ----------------------
+def _product_msb_first(factors):
+    f = np.asarray(factors, dtype=np.complex128).reshape(-1, 2)
+    psi = np.ones(1, dtype=np.complex128)
+    for t in range(f.shape[0]):
+        psi = np.kron(psi, f[t])  # qubit 0 ends up on the most significant bit
+    return psi
+
+
+def _product_alpha_beta_swapped(factors):
+    f = np.asarray(factors, dtype=np.complex128).reshape(-1, 2)[:, ::-1]
+    psi = np.ones(1, dtype=np.complex128)
+    for t in range(f.shape[0]):
+        psi = np.kron(f[t], psi)
+    return psi
+
+
+def _product_conjugated(factors):
+    return np.conj(oracle.product_state(factors))
+
+
+def product_pins_detect(fn):
+    """The product-state pins of test_oracle_pins (one-qubit preparations through the pair update, basis
+    factors), replayed against `fn`; True if any fails."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 3
+    us = [C.haar_u2(rng) for _ in range(n)]
+    want = oracle.basis_state(n, 0)
+    for t, u in enumerate(us):
+        oracle.apply_gate(want, u, t)
+    if np.max(np.abs(fn([u[:, 0] for u in us]) - want)) >= 1e-14:
+        return True
+    x = 0b110
+    return not np.array_equal(fn([(0, 1) if (x >> t) & 1 else (1, 0) for t in range(n)]), oracle.basis_state(n, x))
+
+
+def test_product_state_pins_pass_and_catch_slips():
+    assert not product_pins_detect(oracle.product_state)
+    for fn in (_product_msb_first, _product_alpha_beta_swapped, _product_conjugated):
+        assert product_pins_detect(fn), fn.__name__

@@ -149,6 +149,46 @@ def test_tensor_product_two_qubits():
         assert abs(psi[int(idx)] - f[left] * f[right]) < 1e-15
 
 
+def test_product_state_matches_paper_two_qubit_example():
+    """oracle.product_state against the same worked example: qubit 1 in (a0, b0), qubit 0 in (a1, b1)."""
+    u0, u1 = C.haar_u2(RNG), C.haar_u2(RNG)
+    a0, b0 = u0[:, 0]
+    a1, b1 = u1[:, 0]
+    f = {"a0": a0, "b0": b0, "a1": a1, "b1": b1}
+    psi = oracle.product_state([(a1, b1), (a0, b0)])
+    for idx, left, right in golden_lines("tensor_product_2q.txt"):
+        assert abs(psi[int(idx)] - f[left] * f[right]) < 1e-15
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 9])
+def test_product_state_equals_one_qubit_preparations(n):
+    """Sec. V: the product state equals |0...0> after a one-qubit preparation unitary on each qubit (the pair
+    update of Algorithm 1, an independent route), and its norm is the product of the factors' norms (1)."""
+    us = [C.haar_u2(RNG) for _ in range(n)]
+    want = oracle.basis_state(n, 0)
+    for t, u in enumerate(us):
+        oracle.apply_gate(want, u, t)
+    got = oracle.product_state([u[:, 0] for u in us])
+    assert np.max(np.abs(got - want)) < 1e-14
+    assert abs(oracle.norm2(got) - 1.0) < 1e-14
+    # amplitude k is the product of the per-qubit entries selected by the bits of k (qubit 0 = bit 0)
+    for k in RNG.integers(0, 2 ** n, 8):
+        p = 1.0 + 0j
+        for t in range(n):
+            p *= us[t][(int(k) >> t) & 1, 0]
+        assert abs(got[int(k)] - p) < 1e-15
+
+
+@pytest.mark.parametrize("n,x", [(1, 1), (4, 0b1010), (7, 77)])
+def test_product_state_closed_forms(n, x):
+    """Basis factors give |x> exactly; |+> on every qubit gives the uniform state 2^(-n/2)."""
+    basis = oracle.product_state([(0, 1) if (x >> t) & 1 else (1, 0) for t in range(n)])
+    assert np.array_equal(basis, oracle.basis_state(n, x))
+    h = 1 / math.sqrt(2)
+    plus = oracle.product_state([(h, h)] * n)
+    assert np.max(np.abs(plus - 2.0 ** (-n / 2))) < 1e-15
+
+
 def test_non_sequential_storage_example():
     """Sec. VI.B: interchanging index bits 1 and 2 of an n = 3 vector stores alpha_0,1,4,5,2,3,6,7."""
     order = [int(v) for v in golden_lines("nonsequential_order_n3.txt")[0]]
