@@ -384,7 +384,10 @@ def run_ours(args):
     f64_peak = 152 * 1.73 * sm_hz * 1e6 / 1e12  # measured FP64 multiply-adds per clock per SM
     f64_achieved = f64_fma_launch / (avg_ms * 1e-3) / 1e12 if c128["fused_launches"] else None
     traffic = committed_traffic(args.n)
-    launches_per_step = 1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
+    # init, passes, sweeps, bit-permutation passes, the two norm kernels, and the two product-start kernels
+    folded_start = c128["stats"]["absorbed"] > 0
+    launches_per_step = (1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
+                         + (2 if folded_start else 0))
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
 
     if RANK != 0:
@@ -432,10 +435,11 @@ def run_ours(args):
         "sweep_roofline": sweeps,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "gates/s",
-                "h2d_bytes_per_step": (st["fused_gates"] + st["sweep_gates"]) * 192,
+                "h2d_bytes_per_step": (st["fused_gates"] + st["sweep_gates"]) * 192 + (96 * args.n if st["absorbed"] else 0),
                 "d2h_bytes_per_step": 8 + READ_COUNT * 16,
                 "note": "h2d: the planned 192-byte device gate records, uploaded per step (a single-gate sweep "
-                        "takes its record as a kernel parameter); d2h: the FP64 norm and 1024 amplitudes"},
+                        "takes its record as a kernel parameter), plus 96 B per qubit of product-start factors; "
+                        "d2h: the FP64 norm and 1024 amplitudes"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": c128["clocks"],
         "norm_last_step": c128["norm"],
