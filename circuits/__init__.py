@@ -9,12 +9,15 @@ Qubit convention (the paper's stride rule, Sec. V.A, Eq. for the strided pair up
 
 Gate record (96 bytes, identical to ``sv_gate`` in ``include/sv.h``)::
 
-    U[8]        float64   row-major q11, q12, q21, q22 as (re, im) pairs
-    kind        int32     GATE_U (0) or GATE_SWAP (1)
-    target      int32     target qubit (first qubit of a SWAP)
-    target2     int32     second qubit of a SWAP, -1 otherwise
+    U[8]        float64   row-major q11, q12, q21, q22 as (re, im) pairs (a row of V for GATE_U4 / GATE_U4_ROW)
+    kind        int32     GATE_U (0), GATE_SWAP (1), GATE_U4 (2) or GATE_U4_ROW (3)
+    target      int32     target qubit (first qubit of a SWAP; qubit of index bit b0 of a two-qubit gate)
+    target2     int32     second qubit of a SWAP or two-qubit gate (bit b1), -1 otherwise
     ncontrols   int32     number of control qubits (0..4)
     controls[4] int32     control qubits; a gate acts only where every control bit is 1 (Sec. V.B)
+
+A dense two-qubit gate V (4x4, entry order b0 + 2 b1) takes four consecutive records: GATE_U4 with row 0,
+then three GATE_U4_ROW records with rows 1..3 (same targets, no controls).
 """
 from __future__ import annotations
 
@@ -25,6 +28,8 @@ import numpy as np
 
 GATE_U = 0
 GATE_SWAP = 1
+GATE_U4 = 2
+GATE_U4_ROW = 3
 MAX_CONTROLS = 4
 
 GATE_DTYPE = np.dtype(
@@ -84,7 +89,8 @@ def unpack_u(rec) -> np.ndarray:
 
 @dataclass
 class Gate:
-    """One gate before packing: a 2x2 unitary on ``target`` under ``controls``, or a SWAP."""
+    """One gate before packing: a 2x2 unitary on ``target`` under ``controls``, a SWAP, or a dense 4x4 unitary
+    on (``target``, ``target2``) under ``controls``."""
     kind: int
     target: int
     u: np.ndarray | None = None
@@ -96,6 +102,12 @@ def gate_u(u, target: int, controls=()) -> Gate:
     return Gate(GATE_U, int(target), np.asarray(u, dtype=np.complex128).reshape(2, 2), -1, tuple(int(c) for c in controls))
 
 
+def gate_u4(v, q0: int, q1: int, controls=()) -> Gate:
+    """Dense two-qubit gate: v (4x4) indexed by b0 + 2 b1, b0 = bit of q0, b1 = bit of q1."""
+    return Gate(GATE_U4, int(q0), np.asarray(v, dtype=np.complex128).reshape(4, 4), int(q1),
+                tuple(int(c) for c in controls))
+
+
 def gate_swap(a: int, b: int) -> Gate:
     return Gate(GATE_SWAP, int(a), None, int(b), ())
 
@@ -104,10 +116,16 @@ def cnot(control: int, target: int) -> Gate:
     return gate_u(X, target, (control,))
 
 
+def _row(v: np.ndarray, r: int) -> np.ndarray:
+    return np.array([[x.real, x.imag] for x in v[r]], dtype=np.float64).ravel()
+
+
 def pack(gates) -> np.ndarray:
-    """List of :class:`Gate` -> contiguous structured array of 96-byte records."""
-    out = np.zeros(len(gates), dtype=GATE_DTYPE)
-    for i, g in enumerate(gates):
+    """List of :class:`Gate` -> contiguous structured array of 96-byte records (four per two-qubit gate)."""
+    count = sum(4 if g.kind == GATE_U4 else 1 for g in gates)
+    out = np.zeros(count, dtype=GATE_DTYPE)
+    i = 0
+    for g in gates:
         r = out[i]
         r["kind"] = g.kind
         r["target"] = g.target
@@ -119,18 +137,41 @@ def pack(gates) -> np.ndarray:
         r["controls"] = ctl
         if g.kind == GATE_U:
             r["U"] = _pack_u(g.u)
+        elif g.kind == GATE_U4:
+            r["U"] = _row(g.u, 0)
+            for row in range(1, 4):
+                c = out[i + row]
+                c["kind"] = GATE_U4_ROW
+                c["target"], c["target2"], c["ncontrols"] = g.target, g.target2, 0
+                c["controls"] = [-1] * MAX_CONTROLS
+                c["U"] = _row(g.u, row)
+            i += 3
+        i += 1
     return out
+
+
+def unpack_u4(recs) -> np.ndarray:
+    """4x4 matrix of a two-qubit gate from its four records."""
+    return np.array([[recs[r]["U"][2 * c] + 1j * recs[r]["U"][2 * c + 1] for c in range(4)] for r in range(4)])
 
 
 def unpack(arr: np.ndarray):
     """Structured array -> list of :class:`Gate`."""
     res = []
-    for r in arr:
-        if int(r["kind"]) == GATE_SWAP:
+    i = 0
+    while i < len(arr):
+        r = arr[i]
+        kind = int(r["kind"])
+        nc = int(r["ncontrols"])
+        if kind == GATE_SWAP:
             res.append(gate_swap(int(r["target"]), int(r["target2"])))
+        elif kind == GATE_U4:
+            res.append(gate_u4(unpack_u4(arr[i:i + 4]), int(r["target"]), int(r["target2"]),
+                               tuple(int(c) for c in r["controls"][:nc])))
+            i += 3
         else:
-            nc = int(r["ncontrols"])
             res.append(gate_u(unpack_u(r), int(r["target"]), tuple(int(c) for c in r["controls"][:nc])))
+        i += 1
     return res
 
 
@@ -142,13 +183,22 @@ def inverse(arr: np.ndarray) -> np.ndarray:
         if g.kind == GATE_SWAP:
             inv.append(g)
         else:
-            inv.append(Gate(GATE_U, g.target, g.u.conj().T.copy(), -1, g.controls))
+            inv.append(Gate(g.kind, g.target, g.u.conj().T.copy(), g.target2, g.controls))
     return pack(inv)
 
 
 # ----------------------------------------------------------------------------------------------------------------
 # Circuits
 # ----------------------------------------------------------------------------------------------------------------
+
+def haar_u4(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random 4x4 unitary: QR of a complex Ginibre matrix with the phases of R's diagonal moved into Q
+    (Mezzadri 2007)."""
+    z = (rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))
+
 
 def haar_u2(rng: np.random.Generator) -> np.ndarray:
     """Haar-distributed U(2): QR of a complex Ginibre matrix with the phases of R's diagonal divided out

@@ -55,15 +55,23 @@ typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_F64 = 1, SV_ARITH_DF32 = 2 } sv_arith
 #define SV_MAX_CONTROLS 4
 #define SV_GATE_U 0     /* 2x2 unitary on `target`, acting where every control bit is 1 (Sec. V.B) */
 #define SV_GATE_SWAP 1  /* exchange qubits `target` and `target2` (Sec. VI.B's relabelling) */
+#define SV_GATE_U4 2    /* dense two-qubit unitary V (4x4) on qubits `target` and `target2`, acting where every
+                           control bit is 1; V is indexed by b0 + 2 b1 with b0 the bit of `target` and b1 the
+                           bit of `target2` (so V = A (x) B applies A to target2 and B to target, and the
+                           paper's CNOT matrix of Sec. II.B is V with target2 = control).  Four consecutive
+                           records: this one holds row 0 of V in U, the next three (SV_GATE_U4_ROW) rows 1..3. */
+#define SV_GATE_U4_ROW 3 /* continuation record of SV_GATE_U4: U = row r of V (4 complex entries); target and
+                            target2 repeat the first record's, ncontrols = 0 */
 
 /* One gate record, 96 bytes. */
 typedef struct sv_gate {
-    double U[8];                       /* q11, q12, q21, q22 as (re, im); ignored for SV_GATE_SWAP */
-    int32_t kind;                      /* SV_GATE_U or SV_GATE_SWAP */
+    double U[8];                       /* q11, q12, q21, q22 as (re, im); a row of V for SV_GATE_U4[_ROW];
+                                          ignored for SV_GATE_SWAP */
+    int32_t kind;                      /* SV_GATE_U, SV_GATE_SWAP, SV_GATE_U4 or SV_GATE_U4_ROW */
     int32_t target;                    /* target qubit, 0 <= target < n */
-    int32_t target2;                   /* second SWAP qubit; ignored (set -1) for SV_GATE_U */
+    int32_t target2;                   /* second qubit of SV_GATE_SWAP / SV_GATE_U4; -1 for SV_GATE_U */
     int32_t ncontrols;                 /* 0..SV_MAX_CONTROLS */
-    int32_t controls[SV_MAX_CONTROLS]; /* distinct, != target, < n */
+    int32_t controls[SV_MAX_CONTROLS]; /* distinct, != target (and target2), < n */
 } sv_gate;
 
 typedef struct sv_state sv_state;
@@ -155,6 +163,13 @@ sv_status sv_canonicalize(sv_state *s);
  * Errors: SV_ERR_ARG (qubit out of range, control == target, duplicate controls, > SV_MAX_CONTROLS),
  *         SV_ERR_NOT_UNITARY, SV_ERR_CUDA. */
 sv_status sv_apply_gate(sv_state *s, const double *U, int target, const int *controls, int ncontrols);
+
+/* Dense two-qubit unitary V (16 complex entries, row-major (re, im): 32 doubles) on qubits q0 (index bit b0)
+ * and q1 (bit b1), entry order b0 + 2 b1, under `ncontrols` controls (see SV_GATE_U4).  Both qubits are brought
+ * into the chunk of one fused pass and each quadruple of amplitudes is multiplied by V.
+ * Errors: SV_ERR_ARG (qubits out of range or repeated), SV_ERR_NOT_UNITARY (max |V^dagger V - I| > 1e-10),
+ *         SV_ERR_CUDA. */
+sv_status sv_apply_gate2q(sv_state *s, const double *V, int q0, int q1, const int *controls, int ncontrols);
 
 /* SWAP of qubits a and b.  Done as a relabelling of the layout map (no data movement) unless the state is
  * canonical-only (buffer states), where an in-place bit-swap pass runs. */

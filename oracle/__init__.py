@@ -52,6 +52,7 @@ def _load():
             lib.oracle_gate_size.restype = ctypes.c_int
             lib.oracle_init_basis.argtypes = [ctypes.c_int, P, ctypes.c_uint64]
             lib.oracle_apply_gate.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int]
+            lib.oracle_apply_gate4.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
             lib.oracle_apply_swap.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
             lib.oracle_apply_circuit.argtypes = [ctypes.c_int, P, P, ctypes.c_uint64, ctypes.c_int]
             lib.oracle_norm2.argtypes = [ctypes.c_int, P]
@@ -99,6 +100,19 @@ def apply_gate(psi: np.ndarray, u, target: int, controls=()) -> np.ndarray:
                                    ctl.ctypes.data if ctl.size else None, int(ctl.size))
     if rc != 0:
         raise ValueError(f"oracle_apply_gate rejected the gate (rc={rc})")
+    return psi
+
+
+def apply_gate4(psi: np.ndarray, v, q0: int, q1: int, controls=()) -> np.ndarray:
+    """Apply a (controlled) dense two-qubit gate in place (v: 4x4, entry order b0 + 2 b1); returns ``psi``."""
+    n = _nqubits(psi)
+    v = np.asarray(v, dtype=np.complex128).reshape(4, 4)
+    V = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1).reshape(32))
+    ctl = np.ascontiguousarray(np.asarray(controls, dtype=np.int32))
+    rc = _load().oracle_apply_gate4(n, psi.ctypes.data, V.ctypes.data, int(q0), int(q1),
+                                    ctl.ctypes.data if ctl.size else None, int(ctl.size))
+    if rc != 0:
+        raise ValueError(f"oracle_apply_gate4 rejected the gate (rc={rc})")
     return psi
 
 

@@ -15,6 +15,11 @@
  * SWAP of qubits a and b exchanges alpha_k and alpha_{k xor 2^a xor 2^b} wherever bit a of k is 1 and bit b
  * is 0; Sec. VI.B's "non-sequential storage" example (n = 3, order 0,1,4,5,2,3,6,7) is SWAP(1, 2).
  *
+ * A two-qubit gate (Sec. II.B: multi-qubit gates such as CNOT act as 4x4 matrices on the four basis states
+ * of their qubits) is a 4x4 matrix V on qubits q0 and q1: for every index k whose bits q0 and q1 are 0 (and
+ * whose control bits are all 1), the four amplitudes alpha_{k + b0 2^q0 + b1 2^q1} form a vector a indexed by
+ * j = b0 + 2 b1, replaced by V a (old values on the right, the sum over j taken in order 0..3).
+ *
  * Plain C99, IEEE double, no fused multiply-add (built with -ffp-contract=off), no reordering beyond the
  * loop order above.  The amplitudes are stored interleaved (re, im) in a double array of length 2^(n+1).
  *
@@ -33,6 +38,8 @@
 
 #define KIND_U 0
 #define KIND_SWAP 1
+#define KIND_U4 2
+#define KIND_U4_ROW 3
 
 /* Byte layout of one gate record: 96 bytes, the same as the input generator's record. */
 typedef struct {
@@ -111,6 +118,50 @@ static int apply_swap(int n, double *psi, int qa, int qb)
     return ORACLE_OK;
 }
 
+/* Two-qubit gate: V holds 16 complex entries row-major as (re, im); entry (r, j) multiplies the amplitude whose
+ * (b0, b1) spell j = b0 + 2 b1 into the output whose bits spell r. */
+static int apply_u4(int n, double *psi, const double *V, int q0, int q1, const int32_t *controls, int nc)
+{
+    if (q0 < 0 || q0 >= n || q1 < 0 || q1 >= n || q0 == q1 || nc < 0 || nc > 4) return ORACLE_ERR_ARG;
+    uint64_t cmask = 0;
+    for (int i = 0; i < nc; ++i) {
+        if (controls[i] < 0 || controls[i] >= n || controls[i] == q0 || controls[i] == q1) return ORACLE_ERR_ARG;
+        if (cmask & ((uint64_t)1 << controls[i])) return ORACLE_ERR_ARG;
+        cmask |= (uint64_t)1 << controls[i];
+    }
+    const uint64_t dim = (uint64_t)1 << n;
+    const uint64_t m0 = (uint64_t)1 << q0, m1 = (uint64_t)1 << q1;
+    for (uint64_t k = 0; k < dim; ++k) {
+        if (k & (m0 | m1)) continue;                     /* k = the member of the quadruple with b0 = b1 = 0 */
+        if (cmask != (k & cmask)) continue;              /* every control bit must be 1 */
+        uint64_t idx[4];
+        double ar[4], ai[4];
+        for (int j = 0; j < 4; ++j) {
+            idx[j] = k | ((j & 1) ? m0 : 0) | ((j & 2) ? m1 : 0);
+            ar[j] = psi[2 * idx[j]];
+            ai[j] = psi[2 * idx[j] + 1];
+        }
+        for (int r = 0; r < 4; ++r) {
+            double sr = 0.0, si = 0.0;
+            for (int j = 0; j < 4; ++j) {
+                const double vr = V[8 * r + 2 * j], vi = V[8 * r + 2 * j + 1];
+                sr = sr + (vr * ar[j] - vi * ai[j]);
+                si = si + (vr * ai[j] + vi * ar[j]);
+            }
+            psi[2 * idx[r]] = sr;
+            psi[2 * idx[r] + 1] = si;
+        }
+    }
+    return ORACLE_OK;
+}
+
+int oracle_apply_gate4(int n, double *psi, const double *V, int q0, int q1, const int32_t *controls, int ncontrols)
+{
+    if (n < 1 || n > 40 || psi == NULL || V == NULL) return ORACLE_ERR_ARG;
+    if (ncontrols > 0 && controls == NULL) return ORACLE_ERR_ARG;
+    return apply_u4(n, psi, V, q0, q1, controls, ncontrols);
+}
+
 int oracle_apply_gate(int n, double *psi, const double *U, int target, const int32_t *controls, int ncontrols)
 {
     if (n < 1 || n > 40 || psi == NULL || U == NULL) return ORACLE_ERR_ARG;
@@ -133,6 +184,17 @@ int oracle_apply_circuit(int n, double *psi, const oracle_gate *g, uint64_t ngat
         int rc;
         if (g[i].kind == KIND_SWAP) rc = apply_swap(n, psi, g[i].target, g[i].target2);
         else if (g[i].kind == KIND_U) rc = apply_u(n, psi, g[i].U, g[i].target, g[i].controls, g[i].ncontrols, nthreads);
+        else if (g[i].kind == KIND_U4 && i + 3 < ngates) {
+            /* the matrix's four rows come from this record and the next three */
+            double V[32];
+            rc = ORACLE_OK;
+            for (int r = 0; r < 4; ++r) {
+                if (r > 0 && g[i + r].kind != KIND_U4_ROW) rc = ORACLE_ERR_ARG;
+                memcpy(V + 8 * r, g[i + r].U, sizeof(double) * 8);
+            }
+            if (rc == ORACLE_OK) rc = apply_u4(n, psi, V, g[i].target, g[i].target2, g[i].controls, g[i].ncontrols);
+            if (rc == ORACLE_OK) i += 3;
+        }
         else rc = ORACLE_ERR_ARG;
         if (rc != ORACLE_OK) return -(int)(i + 2);
     }

@@ -11,7 +11,7 @@ import pytest
 
 import circuits as C
 import oracle
-from test_oracle_pins import dense_gate, dense_swap
+from test_oracle_pins import dense_gate, dense_gate4, dense_swap
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "sv_oracle.c")
 
@@ -23,6 +23,12 @@ MUTANTS = {
     "any_control_instead_of_all": ("if ((k & cmask) != cmask) continue;", "if (cmask && (k & cmask) == 0) continue;"),
     "reads_updated_value": ("b[0] = (q21r * ar - q21i * ai)", "b[0] = (q21r * a[0] - q21i * ai)"),
     "swap_condition": ("if ((k & ma) && !(k & mb)) {", "if (k & ma) {"),
+    "u4_qubit_roles": ("idx[j] = k | ((j & 1) ? m0 : 0) | ((j & 2) ? m1 : 0);",
+                       "idx[j] = k | ((j & 1) ? m1 : 0) | ((j & 2) ? m0 : 0);"),
+    "u4_transposed": ("const double vr = V[8 * r + 2 * j], vi = V[8 * r + 2 * j + 1];",
+                      "const double vr = V[8 * j + 2 * r], vi = V[8 * j + 2 * r + 1];"),
+    "u4_controls_ignored": ("if (cmask != (k & cmask)) continue;", "if (0) continue;"),
+    "u4_conjugated": ("si = si + (vr * ai[j] + vi * ar[j]);", "si = si + (vr * ai[j] - vi * ar[j]);"),
 }
 
 
@@ -38,6 +44,7 @@ def build_mutant(tmp_path, name):
     lib = ctypes.CDLL(str(so))
     P = ctypes.c_void_p
     lib.oracle_apply_gate.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int]
+    lib.oracle_apply_gate4.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
     lib.oracle_apply_swap.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
     return lib
 
@@ -57,6 +64,16 @@ def pins_detect(lib) -> bool:
             lib.oracle_apply_gate(n, got.ctypes.data, U.ctypes.data, t, c.ctypes.data if c.size else None, c.size)
             if np.max(np.abs(got - want)) > 1e-12:
                 return True
+    for q0, q1, ctl in [(0, 2, ()), (3, 1, ()), (1, 2, (0,)), (2, 0, (3, 1))]:
+        v = C.haar_u4(rng)
+        psi = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+        want = dense_gate4(n, v, q0, q1, ctl) @ psi
+        got = psi.copy()
+        V = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1).reshape(32))
+        c = np.array(ctl, dtype=np.int32)
+        lib.oracle_apply_gate4(n, got.ctypes.data, V.ctypes.data, q0, q1, c.ctypes.data if c.size else None, c.size)
+        if np.max(np.abs(got - want)) > 1e-12:
+            return True
     for a, b in [(0, 2), (3, 1)]:
         psi = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
         got = psi.copy()
@@ -76,6 +93,7 @@ def test_unmutated_copy_passes(tmp_path):
     lib = ctypes.CDLL(str(so))
     P = ctypes.c_void_p
     lib.oracle_apply_gate.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int]
+    lib.oracle_apply_gate4.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
     lib.oracle_apply_swap.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
     assert not pins_detect(lib)
 

@@ -52,6 +52,26 @@ def dense_swap(n, a, b):
     return c_ab @ c_ba @ c_ab
 
 
+def dense_gate4(n, v, q0, q1, controls=()):
+    """The 2^n x 2^n operator of a (controlled) two-qubit gate written out element by element from its
+    definition (Sec. II.B: a 4x4 matrix on the four basis states of its qubits): <i|O|j> = v[r(i), r(j)] with
+    r(k) = b0 + 2 b1 the gate's bits of k, when i and j agree outside q0 and q1 and every control bit of j is 1;
+    the identity on the other columns."""
+    dim = 2 ** n
+    m = (1 << q0) | (1 << q1)
+    cm = sum(1 << c for c in controls)
+    sub = lambda k: ((k >> q0) & 1) + 2 * ((k >> q1) & 1)
+    op = np.zeros((dim, dim), dtype=np.complex128)
+    for j in range(dim):
+        if (j & cm) != cm:
+            op[j, j] = 1.0
+            continue
+        for i in range(dim):
+            if (i & ~m) == (j & ~m):
+                op[i, j] = v[sub(i), sub(j)]
+    return op
+
+
 def rand_state(n):
     v = RNG.standard_normal(2 ** n) + 1j * RNG.standard_normal(2 ** n)
     return v / np.linalg.norm(v)
@@ -187,6 +207,54 @@ def test_product_state_closed_forms(n, x):
     h = 1 / math.sqrt(2)
     plus = oracle.product_state([(h, h)] * n)
     assert np.max(np.abs(plus - 2.0 ** (-n / 2))) < 1e-15
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_two_qubit_gate_matches_its_operator(n):
+    """Every ordered pair of qubits, with and without controls, against the element-wise operator."""
+    for q0 in range(n):
+        for q1 in range(n):
+            if q0 == q1:
+                continue
+            rest = [q for q in range(n) if q not in (q0, q1)]
+            for ctl in ([()] + ([tuple(rest[:1])] if rest else []) + ([tuple(rest[:2])] if len(rest) > 1 else [])):
+                v = C.haar_u4(RNG)
+                psi = rand_state(n)
+                want = dense_gate4(n, v, q0, q1, ctl) @ psi
+                got = oracle.apply_gate4(psi.copy(), v, q0, q1, ctl)
+                assert np.max(np.abs(got - want)) < 1e-14
+
+
+def test_two_qubit_kronecker_gate_is_two_one_qubit_gates():
+    """Eq. tensor-product-gates: (A (x) B) on (q0, q1) = B on q0 then A on q1 (the pair update)."""
+    n = 5
+    for q0, q1 in [(0, 1), (3, 1), (4, 0)]:
+        a, b = C.haar_u2(RNG), C.haar_u2(RNG)
+        psi = rand_state(n)
+        want = oracle.apply_gate(oracle.apply_gate(psi.copy(), b, q0), a, q1)
+        got = oracle.apply_gate4(psi.copy(), np.kron(a, b), q0, q1)
+        assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_paper_cnot_matrix_as_two_qubit_gate():
+    """The CNOT matrix of Sec. II.B (its truth table in tests/golden/cnot_truth_table.txt: the first ket symbol
+    is the control, index bit 1) as a dense gate with q1 = control equals the controlled X, exactly."""
+    v = np.zeros((4, 4))
+    for inp, out in golden_lines("cnot_truth_table.txt"):
+        v[int(out, 2), int(inp, 2)] = 1.0
+    n = 4
+    for control, target in [(1, 0), (0, 3), (3, 2)]:
+        psi = rand_state(n)
+        want = oracle.apply_gate(psi.copy(), C.X, target, (control,))
+        got = oracle.apply_gate4(psi.copy(), v, target, control)
+        assert np.array_equal(got, want)
+    # the same through packed records (four per gate) and the circuit entry point
+    psi = rand_state(n)
+    w = C.pack([C.gate_u4(v, 0, 1), C.gate_u(C.H, 2), C.gate_u4(C.haar_u4(RNG), 2, 3, (0,))])
+    step = oracle.apply_gate(oracle.apply_gate4(psi.copy(), v, 0, 1), C.H, 2)
+    g = C.unpack(w)[2]
+    step = oracle.apply_gate4(step, g.u, 2, 3, (0,))
+    assert np.array_equal(oracle.apply_circuit(psi.copy(), w), step)
 
 
 def test_non_sequential_storage_example():
