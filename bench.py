@@ -470,8 +470,11 @@ def gates_after_product_start(gates, n):
         if kind == C.GATE_SWAP and not touched[t] and not touched[int(g["target2"])]:
             folded += 1
             continue
+        if kind == C.GATE_U4_ROW:
+            keep.append(g)
+            continue
         touched[t] = True
-        if kind == C.GATE_SWAP:
+        if kind in (C.GATE_SWAP, C.GATE_U4):
             touched[int(g["target2"])] = True
         for c in range(int(g["ncontrols"])):
             touched[int(g["controls"][c])] = True

@@ -44,10 +44,12 @@ SV_OPT_PRODUCT_START = 9
 
 SV_GATE_U = 0
 SV_GATE_SWAP = 1
+SV_GATE_U4 = 2
+SV_GATE_U4_ROW = 3
 
 EXPORTED = [
     "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_init_product", "sv_write_amplitudes", "sv_set_option",
-    "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_swap", "sv_apply_circuit",
+    "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_gate2q", "sv_apply_swap", "sv_apply_circuit",
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version",
@@ -87,6 +89,7 @@ def load(path: str | None = None):
         "sv_get_layout": [P, P],
         "sv_canonicalize": [P],
         "sv_apply_gate": [P, P, i, P, i],
+        "sv_apply_gate2q": [P, P, i, i, P, i],
         "sv_apply_swap": [P, i, i],
         "sv_apply_circuit": [P, P, sz],
         "sv_apply_circuit_graph": [P, P, sz],
@@ -198,6 +201,14 @@ def sv_apply_gate(h: int, u, target: int, controls=()) -> None:
     U = np.ascontiguousarray(np.stack([u.real, u.imag], axis=-1).reshape(8))
     c = np.ascontiguousarray(np.asarray(controls, dtype=np.int32))
     _check(load().sv_apply_gate(h, U.ctypes.data, target, c.ctypes.data if c.size else None, int(c.size)))
+
+
+def sv_apply_gate2q(h: int, v, q0: int, q1: int, controls=()) -> None:
+    """Dense two-qubit gate v (4x4, entry order b0 + 2 b1 with b0 the bit of q0)."""
+    v = np.asarray(v, dtype=np.complex128).reshape(4, 4)
+    V = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1).reshape(32))
+    c = np.ascontiguousarray(np.asarray(controls, dtype=np.int32))
+    _check(load().sv_apply_gate2q(h, V.ctypes.data, q0, q1, c.ctypes.data if c.size else None, int(c.size)))
 
 
 def sv_apply_swap(h: int, a: int, b: int) -> None:

@@ -268,9 +268,11 @@ int absorb_leading(int n, const sv_gate *gates, size_t ngates, std::vector<doubl
       continue;
     }
     touched[g.target] = 1;
-    if (g.kind == SV_GATE_SWAP) touched[g.target2] = 1;
+    if (g.kind == SV_GATE_SWAP || g.kind == SV_GATE_U4) touched[g.target2] = 1;
     for (int c = 0; c < g.ncontrols; ++c) touched[g.controls[c]] = 1;
     rest.push_back(g);
+    if (g.kind == SV_GATE_U4)  // its three row records go along (validated: they follow)
+      for (int r = 1; r < 4; ++r) rest.push_back(gates[++i]);
   }
   return folded;
 }
@@ -493,10 +495,11 @@ sv_status sv_canonicalize(sv_state *s) {
 }
 
 static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool single) {
-  for (size_t i = 0; i < ngates; ++i) {
+  {
     std::string why;
-    const int rc = validate_gate(gates[i], s->n, why);
-    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+    size_t bad = 0;
+    const int rc = validate_records(gates, ngates, s->n, why, bad);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
   }
   std::vector<sv_gate> rest;
   const int prc = product_prologue(s, gates, ngates, rest);
@@ -543,6 +546,24 @@ sv_status sv_apply_gate(sv_state *s, const double *U, int target, const int *con
   return apply_records(s, &g, 1, true);
 }
 
+sv_status sv_apply_gate2q(sv_state *s, const double *V, int q0, int q1, const int *controls, int ncontrols) {
+  if (!s || !V) return set_error(SV_ERR_ARG, "NULL argument");
+  if (ncontrols < 0 || ncontrols > SV_MAX_CONTROLS) return set_error(SV_ERR_ARG, "ncontrols out of range");
+  if (ncontrols > 0 && !controls) return set_error(SV_ERR_ARG, "controls is NULL");
+  sv_gate g[4];
+  std::memset(g, 0, sizeof g);
+  for (int r = 0; r < 4; ++r) {
+    std::memcpy(g[r].U, V + 8 * r, sizeof g[r].U);
+    g[r].kind = r == 0 ? SV_GATE_U4 : SV_GATE_U4_ROW;
+    g[r].target = q0;
+    g[r].target2 = q1;
+    for (int i = 0; i < SV_MAX_CONTROLS; ++i) g[r].controls[i] = -1;
+  }
+  g[0].ncontrols = ncontrols;
+  for (int i = 0; i < ncontrols; ++i) g[0].controls[i] = controls[i];
+  return apply_records(s, g, 4, true);
+}
+
 sv_status sv_apply_swap(sv_state *s, int a, int b) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
   sv_gate g;
@@ -564,10 +585,11 @@ sv_status sv_plan_dry_run(int n, sv_dtype dtype, int chunk_k, const sv_gate *gat
   if (n < 1 || n > kMaxQubits) return set_error(SV_ERR_ARG, "n must be in [1, 36]");
   if (bad_dtype(dtype)) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
   if (!gates && ngates) return set_error(SV_ERR_ARG, "gates is NULL");
-  for (size_t i = 0; i < ngates; ++i) {
+  {
     std::string why;
-    const int rc = validate_gate(gates[i], n, why);
-    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+    size_t bad = 0;
+    const int rc = validate_records(gates, ngates, n, why, bad);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
   }
   sv_state tmp;
   tmp.n = n;

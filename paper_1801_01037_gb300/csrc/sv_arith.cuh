@@ -109,6 +109,21 @@ __device__ __forceinline__ dfv df_dot4(q3 q0, dfv x0, q3 q1, dfv x1, q3 q2, dfv 
   return fast_two_sum(s, c);
 }
 
+// Eight terms (one real output of a row of a two-qubit gate), same scheme.
+__device__ __forceinline__ dfv df_dot8(const q3 (&q)[8], const dfv (&x)[8]) {
+  float c = 0.0f, s, e;
+  float p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = df_term(q[i].h, q[i].m, q[i].l, x[i], c);
+  s = p[0];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) {
+    two_sum(s, p[i], s, e);
+    c = __fadd_rn(c, e);
+  }
+  return fast_two_sum(s, c);
+}
+
 __device__ __forceinline__ dfv df_dot2(q3 q0, dfv x0, q3 q1, dfv x1) {
   float c = 0.0f, s, e;
   const float p0 = df_term(q0.h, q0.m, q0.l, x0, c);
@@ -137,8 +152,20 @@ template <> struct Arith<MODE_C64_F32> {
   static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ S one() { return make_float2(1.f, 0.f); }
   static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) c.q[i] = g.qh[i];
+    // two 16-byte loads (DevGate records are 192 bytes, 16-byte aligned)
+    const float4 a = reinterpret_cast<const float4 *>(g.qh)[0], b = reinterpret_cast<const float4 *>(g.qh)[1];
+    c.q[0] = a.x; c.q[1] = a.y; c.q[2] = a.z; c.q[3] = a.w;
+    c.q[4] = b.x; c.q[5] = b.y; c.q[6] = b.z; c.q[7] = b.w;
+  }
+  // One output of a two-qubit gate: sum_j V[r][j] x_j with c = row r (entries j = 0..3 as (re, im)).
+  static __device__ __forceinline__ S row4(const Coef &c, S x0, S x1, S x2, S x3) {
+    const float *q = c.q;
+    S r;
+    r.x = __fmaf_rn(q[0], x0.x, __fmaf_rn(-q[1], x0.y, __fmaf_rn(q[2], x1.x, __fmaf_rn(-q[3], x1.y,
+          __fmaf_rn(q[4], x2.x, __fmaf_rn(-q[5], x2.y, __fmaf_rn(q[6], x3.x, -q[7] * x3.y)))))));
+    r.y = __fmaf_rn(q[0], x0.y, __fmaf_rn(q[1], x0.x, __fmaf_rn(q[2], x1.y, __fmaf_rn(q[3], x1.x,
+          __fmaf_rn(q[4], x2.y, __fmaf_rn(q[5], x2.x, __fmaf_rn(q[6], x3.y, q[7] * x3.x)))))));
+    return r;
   }
   // r = q[j] * a   (q[j] = complex entry j of the matrix: 0 = q11, 1 = q12, 2 = q21, 3 = q22)
   static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
@@ -165,8 +192,22 @@ template <> struct Arith<MODE_C128_F64> {
   static __device__ __forceinline__ S zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ S one() { return make_double2(1.0, 0.0); }
   static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
+    const double2 *v = reinterpret_cast<const double2 *>(g.q);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) c.q[i] = g.q[i];
+    for (int i = 0; i < 4; ++i) {
+      const double2 t = v[i];
+      c.q[2 * i] = t.x;
+      c.q[2 * i + 1] = t.y;
+    }
+  }
+  static __device__ __forceinline__ S row4(const Coef &c, S x0, S x1, S x2, S x3) {
+    const double *q = c.q;
+    S r;
+    r.x = __fma_rn(q[0], x0.x, __fma_rn(-q[1], x0.y, __fma_rn(q[2], x1.x, __fma_rn(-q[3], x1.y,
+          __fma_rn(q[4], x2.x, __fma_rn(-q[5], x2.y, __fma_rn(q[6], x3.x, -q[7] * x3.y)))))));
+    r.y = __fma_rn(q[0], x0.y, __fma_rn(q[1], x0.x, __fma_rn(q[2], x1.y, __fma_rn(q[3], x1.x,
+          __fma_rn(q[4], x2.y, __fma_rn(q[5], x2.x, __fma_rn(q[6], x3.y, q[7] * x3.x)))))));
+    return r;
   }
   static __device__ __forceinline__ S cmul(const Coef &c, int j, S a) {
     const double qr = c.q[2 * j], qi = c.q[2 * j + 1];
@@ -196,8 +237,25 @@ template <> struct Arith<MODE_C128_DF32> {
   static __device__ __forceinline__ S zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ S one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void coef(Coef &c, const DevGate &g) {
+    const float4 *h = reinterpret_cast<const float4 *>(g.qh), *m = reinterpret_cast<const float4 *>(g.qm),
+                 *l = reinterpret_cast<const float4 *>(g.ql);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) { c.h[i] = g.qh[i]; c.m[i] = g.qm[i]; c.l[i] = g.ql[i]; }
+    for (int i = 0; i < 2; ++i) {
+      const float4 a = h[i], b = m[i], d = l[i];
+      c.h[4 * i] = a.x; c.h[4 * i + 1] = a.y; c.h[4 * i + 2] = a.z; c.h[4 * i + 3] = a.w;
+      c.m[4 * i] = b.x; c.m[4 * i + 1] = b.y; c.m[4 * i + 2] = b.z; c.m[4 * i + 3] = b.w;
+      c.l[4 * i] = d.x; c.l[4 * i + 1] = d.y; c.l[4 * i + 2] = d.z; c.l[4 * i + 3] = d.w;
+    }
+  }
+  static __device__ __forceinline__ S row4(const Coef &c, S x0, S x1, S x2, S x3) {
+    const dfv xr[4] = {{x0.x, x0.y}, {x1.x, x1.y}, {x2.x, x2.y}, {x3.x, x3.y}};
+    const dfv xi[4] = {{x0.z, x0.w}, {x1.z, x1.w}, {x2.z, x2.w}, {x3.z, x3.w}};
+    const q3 qre[8] = {e(c, 0), ne(c, 1), e(c, 2), ne(c, 3), e(c, 4), ne(c, 5), e(c, 6), ne(c, 7)};
+    const dfv are[8] = {xr[0], xi[0], xr[1], xi[1], xr[2], xi[2], xr[3], xi[3]};
+    const q3 qim[8] = {e(c, 0), e(c, 1), e(c, 2), e(c, 3), e(c, 4), e(c, 5), e(c, 6), e(c, 7)};
+    const dfv aim[8] = {xi[0], xr[0], xi[1], xr[1], xi[2], xr[2], xi[3], xr[3]};
+    const dfv re = df_dot8(qre, are), im = df_dot8(qim, aim);
+    return make_float4(re.h, re.l, im.h, im.l);
   }
   // Entry e of the matrix (0 = q11 re, 1 = q11 im, ..., 7 = q22 im), optionally negated.
   static __device__ __forceinline__ q3 e(const Coef &c, int i) { return q3{c.h[i], c.m[i], c.l[i]}; }

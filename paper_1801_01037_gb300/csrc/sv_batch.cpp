@@ -24,11 +24,10 @@ int default_mode(sv_dtype dt) { return dt == SV_C64 ? MODE_C64_F32 : MODE_C128_D
 int validate_circuit(int n, const sv_gate *g, size_t ng, std::string &why) {
   if (n < 1 || n > kMaxQubits) { why = "n out of range"; return SV_ERR_ARG; }
   if (!g && ng) { why = "gates is NULL"; return SV_ERR_ARG; }
-  for (size_t i = 0; i < ng; ++i) {
-    std::string w;
-    const int rc = validate_gate(g[i], n, w);
-    if (rc != SV_OK) { why = "gate " + std::to_string(i) + ": " + w; return rc; }
-  }
+  std::string w;
+  size_t bad = 0;
+  const int rc = validate_records(g, ng, n, w, bad);
+  if (rc != SV_OK) { why = "gate " + std::to_string(bad) + ": " + w; return rc; }
   return SV_OK;
 }
 

@@ -69,6 +69,37 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
   }
 }
 
+// All quadruples of the chunk for a dense two-qubit gate (GC_DENSE4 + three GC_ROW records): chunk bits t0
+// (index bit b0 of the gate's matrix) and t1 (b1), local controls cm.  The four outputs are computed from
+// the old values before any is stored.
+template <int MODE>
+__device__ __noinline__ void chunk_quads(typename Arith<MODE>::S *sm, const DevGate *rows, uint32_t nquads, int t0,
+                                            int t1, uint32_t cm) {
+  using M = Arith<MODE>;
+  using S = typename M::S;
+  const int lo = t0 < t1 ? t0 : t1, hi = t0 < t1 ? t1 : t0;
+  const uint32_t b0 = 1u << t0, b1 = 1u << t1;
+  for (uint32_t i = threadIdx.x; i < nquads; i += kFusedThreads) {
+    const uint32_t j = ins0(ins0(i, lo), hi);
+    if ((j & cm) != cm) continue;
+    const uint32_t s0 = slot<MODE>(j), s1 = slot<MODE>(j | b0), s2 = slot<MODE>(j | b1), s3 = slot<MODE>(j | b0 | b1);
+    const S x0 = sm[s0], x1 = sm[s1], x2 = sm[s2], x3 = sm[s3];
+    typename M::Coef cf;
+    M::coef(cf, rows[0]);
+    const S r0 = M::row4(cf, x0, x1, x2, x3);
+    M::coef(cf, rows[1]);
+    const S r1 = M::row4(cf, x0, x1, x2, x3);
+    M::coef(cf, rows[2]);
+    const S r2 = M::row4(cf, x0, x1, x2, x3);
+    M::coef(cf, rows[3]);
+    const S r3 = M::row4(cf, x0, x1, x2, x3);
+    sm[s0] = r0;
+    sm[s1] = r1;
+    sm[s2] = r2;
+    sm[s3] = r3;
+  }
+}
+
 // ---- Complex64 register cubes (GC_CUBE) ----------------------------------------------------------------
 // v[s] holds the amplitude whose cube bits spell s (bit i of s = chunk bit pos[i]).  Each routine applies one
 // gate to the 16 registers with the same arithmetic, in the same order, as the shared-memory pair loop, so
@@ -225,6 +256,13 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const uint64_t gmask = g.gmask;
     if ((base & gmask) != gmask) continue;  // a control bit outside the chunk is 0: the gate skips this chunk
     const uint32_t cls = g.cls;
+    if (cls == GC_ROW) continue;  // consumed with its GC_DENSE4 record
+    if (cls == GC_DENSE4) {
+      chunk_quads<MODE>(sm, p.gates + gi, nloc >> 2, g.target, (int)g.tmask, (uint32_t)g.cmask);
+      gi += 3;
+      __syncthreads();
+      continue;
+    }
     if (cls == GC_CUBE) {
       if constexpr (MODE == MODE_C64_F32) {
         cube_run(p.gates + gi + 1, g.target, (uint32_t)g.cmask, base, sm, k);

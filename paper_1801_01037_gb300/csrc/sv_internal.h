@@ -24,6 +24,9 @@ enum GateClass : uint32_t {
   GC_ANTIDIAG = 3,  // q11 = q22 = 0: alpha_k <- q12 alpha_{k+2^t}, alpha_{k+2^t} <- q21 alpha_k
   GC_X = 4,         // q12 = q21 = 1, q11 = q22 = 0: the pair is exchanged (pure moves)
   GC_CUBE = 5,      // not a gate: header of a register cube (complex64 fused passes, see below)
+  GC_DENSE4 = 6,    // dense two-qubit gate: this record holds row 0 of V, `target` the chunk bit of b0 and
+                    //   `tmask` the chunk bit of b1 (both always inside the chunk); then three GC_ROW records
+  GC_ROW = 7,       // rows 1..3 of the GC_DENSE4 record before it
 };
 
 // Register cube.  Inside a complex64 fused pass, a header DevGate with cls = GC_CUBE says that the next

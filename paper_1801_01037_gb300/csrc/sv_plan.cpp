@@ -103,6 +103,90 @@ int validate_gate(const sv_gate &g, int n, std::string &why) {
   return SV_OK;
 }
 
+// A two-qubit gate: its four records, qubits, controls and the unitarity of V (16 complex entries).
+static int validate_gate4(const sv_gate *g, size_t avail, int n, std::string &why) {
+  char buf[160];
+  if (avail < 4) {
+    why = "two-qubit gate needs three SV_GATE_U4_ROW records after it";
+    return SV_ERR_ARG;
+  }
+  const int q0 = g[0].target, q1 = g[0].target2;
+  for (int r = 1; r < 4; ++r)
+    if (g[r].kind != SV_GATE_U4_ROW || g[r].target != q0 || g[r].target2 != q1 || g[r].ncontrols != 0) {
+      why = "two-qubit gate needs three SV_GATE_U4_ROW records with the same qubits after it";
+      return SV_ERR_ARG;
+    }
+  if (q0 < 0 || q0 >= n || q1 < 0 || q1 >= n || q0 == q1) {
+    snprintf(buf, sizeof buf, "two-qubit gate qubits (%d, %d) must be distinct and in [0, %d)", q0, q1, n);
+    why = buf;
+    return SV_ERR_ARG;
+  }
+  if (g[0].ncontrols < 0 || g[0].ncontrols > SV_MAX_CONTROLS) {
+    snprintf(buf, sizeof buf, "ncontrols %d out of range [0, %d]", g[0].ncontrols, SV_MAX_CONTROLS);
+    why = buf;
+    return SV_ERR_ARG;
+  }
+  uint64_t seen = (1ull << q0) | (1ull << q1);
+  for (int i = 0; i < g[0].ncontrols; ++i) {
+    const int c = g[0].controls[i];
+    if (c < 0 || c >= n || (seen >> c & 1ull)) {
+      snprintf(buf, sizeof buf, "control %d is out of range, equal to a target or repeated", c);
+      why = buf;
+      return SV_ERR_ARG;
+    }
+    seen |= 1ull << c;
+  }
+  double v[32];
+  for (int r = 0; r < 4; ++r) std::memcpy(v + 8 * r, g[r].U, sizeof g[r].U);
+  for (int i = 0; i < 32; ++i)
+    if (!std::isfinite(v[i])) {
+      why = "gate matrix has a non-finite entry";
+      return SV_ERR_NOT_UNITARY;
+    }
+  double worst = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double re = 0, im = 0;  // (V^dagger V)_ij = sum_r conj(V_ri) V_rj
+      for (int r = 0; r < 4; ++r) {
+        const double ar = v[8 * r + 2 * i], ai = -v[8 * r + 2 * i + 1];
+        const double br = v[8 * r + 2 * j], bi = v[8 * r + 2 * j + 1];
+        re += ar * br - ai * bi;
+        im += ar * bi + ai * br;
+      }
+      worst = std::max(worst, std::fabs(re - (i == j ? 1.0 : 0.0)));
+      worst = std::max(worst, std::fabs(im));
+    }
+  if (worst > 1e-10) {
+    snprintf(buf, sizeof buf, "gate matrix is not unitary (max |V^dagger V - I| = %.3g)", worst);
+    why = buf;
+    return SV_ERR_NOT_UNITARY;
+  }
+  return SV_OK;
+}
+
+int validate_records(const sv_gate *g, size_t ngates, int n, std::string &why, size_t &bad) {
+  for (size_t i = 0; i < ngates; ++i) {
+    int rc;
+    if (g[i].kind == SV_GATE_U4) {
+      rc = validate_gate4(g + i, ngates - i, n, why);
+      if (rc == SV_OK) {
+        i += 3;
+        continue;
+      }
+    } else if (g[i].kind == SV_GATE_U4_ROW) {
+      why = "SV_GATE_U4_ROW record without its SV_GATE_U4 record";
+      rc = SV_ERR_ARG;
+    } else {
+      rc = validate_gate(g[i], n, why);
+    }
+    if (rc != SV_OK) {
+      bad = i;
+      return rc;
+    }
+  }
+  return SV_OK;
+}
+
 size_t plan_blob_bytes(const Plan &P) { return P.fused_gates.size() * sizeof(DevGate); }
 
 void plan_blob_fill(const Plan &P, void *dst) {
@@ -200,11 +284,12 @@ std::vector<PassDesc> canonicalize_passes(int n, const PlanConfig &cfg, std::vec
 namespace {
 
 struct Sched {
-  int idx;        // source gate index
+  int idx;        // source gate index (the first record of a two-qubit gate)
   int cls;        // gate class, or -2 (SWAP folded into the layout) / -1 (identity): no device work
   int pt;         // physical target (-1 for SWAP / identity entries)
+  int pt2;        // two-qubit gate: physical bit of b1 (-1 otherwise)
   uint64_t pc;    // physical control mask
-  uint64_t phys;  // physical bits the entry touches (target, controls; both bits of a SWAP)
+  uint64_t phys;  // physical bits the entry touches (target(s), controls; both bits of a SWAP)
   uint64_t logi;  // logical qubits the entry touches
 };
 
@@ -223,17 +308,24 @@ DevGate to_sweep_gate(const sv_gate &g, const Sched &s) {
 } // namespace
 
 // Split a pass's gate run (chunk-local targets) into register cubes, in order: a cube takes gates while the
-// distinct targets of its pairing gates stay within kCubeBits bits; diagonal gates join any cube.  Unused
+// distinct targets of its pairing gates stay within kCubeBits bits; diagonal gates join any cube; a two-qubit
+// gate ends the cube and is left outside any cube.  Unused
 // cube bits are filled from the top of the chunk, which keeps the threads of a half-warp on distinct
 // shared-memory banks for most bit sets.
 void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out) {
   size_t i = 0;
   while (i < run.size()) {
+    if (run[i].cls == GC_DENSE4) {  // two-qubit gates run on their own, from shared memory (4 records)
+      out.insert(out.end(), run.begin() + i, run.begin() + std::min(run.size(), i + 4));
+      i += 4;
+      continue;
+    }
     uint32_t bits = 0;
     int nb = 0;
     size_t j = i;
     for (; j < run.size(); ++j) {
       const DevGate &g = run[j];
+      if (g.cls == GC_DENSE4) break;
       if (!needs_pairing((int)g.cls) || g.target < 0) continue;
       const uint32_t tb = 1u << g.target;
       if (bits & tb) continue;
@@ -256,6 +348,16 @@ void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &o
   }
 }
 
+// Identity check of a two-qubit gate's four records.
+static bool is_identity4(const sv_gate *g) {
+  for (int r = 0; r < 4; ++r)
+    for (int j = 0; j < 4; ++j) {
+      const double re = g[r].U[2 * j], im = g[r].U[2 * j + 1];
+      if (im != 0.0 || re != (r == j ? 1.0 : 0.0)) return false;
+    }
+  return true;
+}
+
 void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &P) {
   P = Plan();
   P.gate_step.assign(ngates, -1);
@@ -264,13 +366,16 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
   const int k = std::min(cfg.k, n);
   int c = std::min(cfg.c, k);
   c = std::max(c, std::min(3, k));
+  if (k < n) c = std::min(c, std::max(std::min(3, k), k - 2));  // room for both bits of a two-qubit gate
 
+  auto records_of = [&](size_t i) { return gates[i].kind == SV_GATE_U4 ? 4 : 1; };
   auto sched_of = [&](size_t i, int cls) {
     Sched s;
     const sv_gate &g = gates[i];
     s.idx = (int)i;
     s.cls = cls;
     s.pc = 0;
+    s.pt2 = -1;
     s.logi = 1ull << g.target;
     if (g.kind == SV_GATE_SWAP) {
       s.pt = -1;
@@ -284,132 +389,33 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
     }
     s.pt = cls == -1 ? -1 : perm[g.target];
     s.phys = s.pc | (1ull << perm[g.target]);
+    if (g.kind == SV_GATE_U4) {
+      s.pt2 = cls == -1 ? -1 : perm[g.target2];
+      s.phys |= 1ull << perm[g.target2];
+      s.logi |= 1ull << g.target2;
+    }
     return s;
   };
-
-  if (!cfg.fusion) {
-    for (size_t i = 0; i < ngates; ++i) {
-      const sv_gate &g = gates[i];
-      P.gate_order[i] = order++;
-      if (g.kind == SV_GATE_SWAP) {
-        std::swap(perm[g.target], perm[g.target2]);
-        ++P.n_relabels;
-        continue;
-      }
-      const int cls = classify(g.U);
-      if (cls < 0) { ++P.n_skipped; continue; }
-      const Sched s = sched_of(i, cls);
-      P.sweep_gates.push_back(to_sweep_gate(g, s));
-      P.gate_step[i] = (int)P.steps.size();
-      P.step_qmask.push_back(1ull << s.pt);
-      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
-      ++P.n_sweep_gates;
-    }
-    return;
-  }
-
-  // Per-qubit queues of the gates touching each qubit; a gate is ready when it heads all of its queues.
-  std::vector<std::vector<int>> q(n);
-  std::vector<int> cls_of(ngates);
-  auto qubits_of = [&](size_t i, int *out) {
-    int m = 0;
-    const sv_gate &g = gates[i];
-    out[m++] = g.target;
-    if (g.kind == SV_GATE_SWAP) out[m++] = g.target2;
-    else
-      for (int j = 0; j < g.ncontrols; ++j) out[m++] = g.controls[j];
-    return m;
+  auto cls_of_record = [&](size_t i) {
+    if (gates[i].kind == SV_GATE_SWAP) return -2;
+    if (gates[i].kind == SV_GATE_U4) return is_identity4(gates + i) ? -1 : (int)GC_DENSE4;
+    return classify(gates[i].U);
   };
-  for (size_t i = 0; i < ngates; ++i) {
-    int qs[6];
-    const int m = qubits_of(i, qs);
-    for (int j = 0; j < m; ++j) q[qs[j]].push_back((int)i);
-    cls_of[i] = gates[i].kind == SV_GATE_SWAP ? -2 : classify(gates[i].U);
-  }
-  std::vector<size_t> head(n, 0);
-  auto is_ready = [&](int i) {
-    int qs[6];
-    const int m = qubits_of(i, qs);
-    for (int j = 0; j < m; ++j)
-      if (head[qs[j]] >= q[qs[j]].size() || q[qs[j]][head[qs[j]]] != i) return false;
-    return true;
+  // Execution-order bookkeeping: a two-qubit gate's four records keep consecutive positions.
+  auto record_order = [&](int idx) {
+    for (int r = 0; r < records_of(idx); ++r) P.gate_order[idx + r] = order++;
   };
-  std::set<int> ready;
-  for (int u = 0; u < n; ++u)
-    if (!q[u].empty() && is_ready(q[u][0])) ready.insert(q[u][0]);
-  auto pop = [&](int i) {
-    ready.erase(i);
-    int qs[6];
-    const int m = qubits_of(i, qs);
-    for (int j = 0; j < m; ++j) ++head[qs[j]];
-    for (int j = 0; j < m; ++j) {
-      const int u = qs[j];
-      if (head[u] < q[u].size() && is_ready(q[u][head[u]])) ready.insert(q[u][head[u]]);
-    }
+  auto record_step = [&](int idx, int step) {
+    for (int r = 0; r < records_of(idx); ++r) P.gate_step[idx + r] = step;
   };
 
-  bool first_pass = true;
-  while (!ready.empty() || (first_pass && cfg.init_first)) {
-    bool inQ[64] = {false};
+  // One fused pass over the chunk bits inQ applying the entries pg (SWAP / identity entries included).
+  auto emit_pass = [&](const bool *inQ_in, const std::vector<Sched> &pg, bool init_here) {
+    bool inQ[64];
     int qcount = 0;
-    if (k == n) {
-      for (int b = 0; b < n; ++b) inQ[b] = true;
-      qcount = n;
-    } else {
-      for (int b = 0; b < c; ++b) inQ[b] = true;
-      qcount = c;
-    }
-    std::vector<Sched> pg;  // entries of this pass in scheduling order (SWAP / identity entries included)
-    int nreal = 0;
-    for (;;) {
-      int chosen = -1;
-      for (int i : ready) {
-        const int cls = cls_of[i];
-        if (cls < 0 || !needs_pairing(cls) || inQ[perm[gates[i].target]]) { chosen = i; break; }
-      }
-      if (chosen >= 0) {
-        const int cls = cls_of[chosen];
-        pg.push_back(sched_of(chosen, cls));
-        if (cls == -2) {
-          std::swap(perm[gates[chosen].target], perm[gates[chosen].target2]);
-          ++P.n_relabels;
-        } else if (cls == -1) {
-          ++P.n_skipped;
-        } else {
-          ++nreal;
-        }
-        pop(chosen);
-        continue;
-      }
-      if (qcount >= k || ready.empty()) break;
-      // Add the physical bit that the most ready gates are waiting for (ties: the earliest gate).
-      int best_bit = -1, best_count = 0;
-      int counts[64] = {0};
-      for (int i : ready) {
-        const int b = perm[gates[i].target];
-        if (++counts[b] > best_count) { best_count = counts[b]; best_bit = b; }
-      }
-      if (best_bit < 0) break;
-      inQ[best_bit] = true;
-      ++qcount;
-    }
-    const bool init_here = first_pass && cfg.init_first;
-    first_pass = false;
-    if (nreal == 0 && !init_here) {
-      for (const Sched &e : pg) P.gate_order[e.idx] = order++;
-      continue;
-    }
-    if (nreal == 1 && cfg.single_as_sweep && !init_here) {
-      for (const Sched &e : pg) {
-        P.gate_order[e.idx] = order++;
-        if (e.cls < 0) continue;
-        P.gate_step[e.idx] = (int)P.steps.size();
-        P.step_qmask.push_back(1ull << e.pt);
-        P.sweep_gates.push_back(to_sweep_gate(gates[e.idx], e));
-        P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
-        ++P.n_sweep_gates;
-      }
-      continue;
+    for (int b = 0; b < n; ++b) {
+      inQ[b] = inQ_in[b];
+      qcount += inQ[b] ? 1 : 0;
     }
     // Fill Q up to k bits with the lowest unused bits, so every pass has chunks of exactly 2^k amplitudes.
     for (int b = 0; b < n && qcount < k; ++b)
@@ -435,21 +441,33 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
     P.pass_gate_offset.push_back((int)P.fused_gates.size());
     int ng = 0;
     for (const Sched &s : pg) {
-      P.gate_order[s.idx] = order++;
+      record_order(s.idx);
       if (s.cls < 0) continue;
-      P.gate_step[s.idx] = step_index;
+      record_step(s.idx, step_index);
       DevGate g;
       std::memset(&g, 0, sizeof g);
       fill_coefficients(g, gates[s.idx].U);
       g.cls = (uint32_t)s.cls;
       if (inQ[s.pt]) g.target = local[s.pt];
       else { g.target = -1; g.tmask = 1ull << s.pt; }
+      if (s.cls == GC_DENSE4) g.tmask = (uint64_t)local[s.pt2];
       for (int b = 0; b < n; ++b)
         if (s.pc >> b & 1ull) {
           if (inQ[b]) g.cmask |= 1ull << local[b];
           else g.gmask |= 1ull << b;
         }
       P.fused_gates.push_back(g);
+      if (s.cls == GC_DENSE4) {
+        for (int r = 1; r < 4; ++r) {
+          DevGate row;
+          std::memset(&row, 0, sizeof row);
+          fill_coefficients(row, gates[s.idx + r].U);
+          row.cls = GC_ROW;
+          row.target = g.target;
+          row.tmask = g.tmask;
+          P.fused_gates.push_back(row);
+        }
+      }
       ++ng;
     }
     if (cfg.cubes && k >= 8 && ng > 0) {
@@ -463,6 +481,153 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
     P.passes.push_back(d);
     P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, ng});
     P.n_fused_gates += ng;
+  };
+  auto low_bits = [&](bool *inQ) {
+    for (int b = 0; b < n; ++b) inQ[b] = (k == n) || b < c;
+  };
+
+  if (!cfg.fusion) {
+    for (size_t i = 0; i < ngates; ++i) {
+      const sv_gate &g = gates[i];
+      if (g.kind == SV_GATE_U4_ROW) continue;
+      if (g.kind == SV_GATE_SWAP) {
+        record_order((int)i);
+        std::swap(perm[g.target], perm[g.target2]);
+        ++P.n_relabels;
+        continue;
+      }
+      const int cls = cls_of_record(i);
+      if (cls < 0) {
+        record_order((int)i);
+        ++P.n_skipped;
+        continue;
+      }
+      const Sched s = sched_of(i, cls);
+      if (cls == GC_DENSE4) {  // no single-gate sweep for a two-qubit gate: a one-gate pass over both bits
+        bool inQ[64];
+        low_bits(inQ);
+        inQ[s.pt] = inQ[s.pt2] = true;
+        emit_pass(inQ, std::vector<Sched>{s}, false);
+        continue;
+      }
+      record_order((int)i);
+      P.sweep_gates.push_back(to_sweep_gate(g, s));
+      record_step((int)i, (int)P.steps.size());
+      P.step_qmask.push_back(1ull << s.pt);
+      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+      ++P.n_sweep_gates;
+    }
+    return;
+  }
+
+  // Per-qubit queues of the gates touching each qubit; a gate is ready when it heads all of its queues.
+  std::vector<std::vector<int>> q(n);
+  std::vector<int> cls_of(ngates, -3);
+  auto qubits_of = [&](size_t i, int *out) {
+    int m = 0;
+    const sv_gate &g = gates[i];
+    out[m++] = g.target;
+    if (g.kind == SV_GATE_SWAP || g.kind == SV_GATE_U4) out[m++] = g.target2;
+    if (g.kind != SV_GATE_SWAP)
+      for (int j = 0; j < g.ncontrols; ++j) out[m++] = g.controls[j];
+    return m;
+  };
+  for (size_t i = 0; i < ngates; ++i) {
+    if (gates[i].kind == SV_GATE_U4_ROW) continue;
+    int qs[8];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j) q[qs[j]].push_back((int)i);
+    cls_of[i] = cls_of_record(i);
+  }
+  std::vector<size_t> head(n, 0);
+  auto is_ready = [&](int i) {
+    int qs[8];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j)
+      if (head[qs[j]] >= q[qs[j]].size() || q[qs[j]][head[qs[j]]] != i) return false;
+    return true;
+  };
+  std::set<int> ready;
+  for (int u = 0; u < n; ++u)
+    if (!q[u].empty() && is_ready(q[u][0])) ready.insert(q[u][0]);
+  auto pop = [&](int i) {
+    ready.erase(i);
+    int qs[8];
+    const int m = qubits_of(i, qs);
+    for (int j = 0; j < m; ++j) ++head[qs[j]];
+    for (int j = 0; j < m; ++j) {
+      const int u = qs[j];
+      if (head[u] < q[u].size() && is_ready(q[u][head[u]])) ready.insert(q[u][head[u]]);
+    }
+  };
+  // Can entry i run in a pass over chunk bits inQ?  Pairing gates need their target bit, two-qubit gates
+  // both bits; diagonal gates, SWAPs and identities fit anywhere.
+  auto fits = [&](int i, const bool *inQ) {
+    const int cls = cls_of[i];
+    if (cls < 0) return true;
+    if (cls == GC_DENSE4) return inQ[perm[gates[i].target]] && inQ[perm[gates[i].target2]];
+    return !needs_pairing(cls) || inQ[perm[gates[i].target]];
+  };
+
+  bool first_pass = true;
+  while (!ready.empty() || (first_pass && cfg.init_first)) {
+    bool inQ[64] = {false};
+    low_bits(inQ);
+    int qcount = 0;
+    for (int b = 0; b < n; ++b) qcount += inQ[b] ? 1 : 0;
+    std::vector<Sched> pg;  // entries of this pass in scheduling order (SWAP / identity entries included)
+    int nreal = 0, ndense4 = 0;
+    for (;;) {
+      int chosen = -1;
+      for (int i : ready)
+        if (fits(i, inQ)) { chosen = i; break; }
+      if (chosen >= 0) {
+        const int cls = cls_of[chosen];
+        pg.push_back(sched_of(chosen, cls));
+        if (cls == -2) {
+          std::swap(perm[gates[chosen].target], perm[gates[chosen].target2]);
+          ++P.n_relabels;
+        } else if (cls == -1) {
+          ++P.n_skipped;
+        } else {
+          ++nreal;
+          ndense4 += cls == GC_DENSE4 ? 1 : 0;
+        }
+        pop(chosen);
+        continue;
+      }
+      if (qcount >= k || ready.empty()) break;
+      // Add the physical bit that the most ready gates are waiting for (ties: the earliest gate).
+      int best_bit = -1, best_count = 0;
+      int counts[64] = {0};
+      for (int i : ready) {
+        int bits[2] = {perm[gates[i].target], cls_of[i] == GC_DENSE4 ? perm[gates[i].target2] : -1};
+        for (int b : bits)
+          if (b >= 0 && !inQ[b] && ++counts[b] > best_count) { best_count = counts[b]; best_bit = b; }
+      }
+      if (best_bit < 0) break;
+      inQ[best_bit] = true;
+      ++qcount;
+    }
+    const bool init_here = first_pass && cfg.init_first;
+    first_pass = false;
+    if (nreal == 0 && !init_here) {
+      for (const Sched &e : pg) record_order(e.idx);
+      continue;
+    }
+    if (nreal == 1 && ndense4 == 0 && cfg.single_as_sweep && !init_here) {
+      for (const Sched &e : pg) {
+        record_order(e.idx);
+        if (e.cls < 0) continue;
+        record_step(e.idx, (int)P.steps.size());
+        P.step_qmask.push_back(1ull << e.pt);
+        P.sweep_gates.push_back(to_sweep_gate(gates[e.idx], e));
+        P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+        ++P.n_sweep_gates;
+      }
+      continue;
+    }
+    emit_pass(inQ, pg, init_here);
   }
 }
 

@@ -59,6 +59,9 @@ int validate_gate(const sv_gate &g, int n, std::string &why);
 // header before each run.  Order is kept; every gate lands in exactly one cube.
 void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out);
 
+// Validate a record sequence (two-qubit gates take four records); on error `bad` is the first bad record.
+int validate_records(const sv_gate *g, size_t ngates, int n, std::string &why, size_t &bad);
+
 // Plan `ngates` validated records; perm (logical -> physical) is read and updated by SWAP relabelling.
 void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &out);
 

@@ -225,10 +225,11 @@ sv_status sv_renormalize(sv_state *s) {
 // Capture the planned launches once per (gates, layout, state, options) and replay the graph afterwards.
 sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngates) {
   if (!s || (!gates && ngates)) return set_error(SV_ERR_ARG, "NULL argument");
-  for (size_t i = 0; i < ngates; ++i) {
+  {
     std::string why;
-    const int rc = validate_gate(gates[i], s->n, why);
-    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(i) + ": " + why);
+    size_t bad = 0;
+    const int rc = validate_records(gates, ngates, s->n, why, bad);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
   }
   std::vector<sv_gate> rest;
   const int prc = product_prologue(s, gates, ngates, rest);

@@ -96,6 +96,27 @@ def test_validation_rejects_bad_gates(lib):
     assert e.value.code == B.SV_ERR_NOT_UNITARY
 
 
+def test_validation_of_two_qubit_records(lib):
+    v = C.haar_u4(np.random.default_rng(4))
+    good = C.pack([C.gate_u4(v, 0, 2, (1,))])
+    B.sv_plan_dry_run(4, B.SV_C128, good)
+    bad = []
+    bad.append(good[:3].copy())                                     # a row record missing
+    bad.append(good[1:].copy())                                     # rows without their first record
+    x = good.copy(); x[2]["target2"] = 3; bad.append(x)             # rows name other qubits
+    x = good.copy(); x[0]["target2"] = 0; x[1:]["target2"] = 0; bad.append(x)  # both qubits the same
+    x = good.copy(); x[0]["controls"][0] = 2; bad.append(x)         # control equal to a target
+    x = good.copy(); x[0]["target"] = 7; x[1:]["target"] = 7; bad.append(x)    # qubit out of range
+    for g in bad:
+        with pytest.raises(B.SvError) as e:
+            B.sv_plan_dry_run(4, B.SV_C128, g)
+        assert e.value.code == B.SV_ERR_ARG
+    x = good.copy(); x[3]["U"][0] += 1e-6                           # not unitary
+    with pytest.raises(B.SvError) as e:
+        B.sv_plan_dry_run(4, B.SV_C128, x)
+    assert e.value.code == B.SV_ERR_NOT_UNITARY
+
+
 def replay_in_plan_order(n, gates, plan):
     """The circuit's gates in the planner's execution order."""
     order = plan["order_of_gate"]
@@ -109,7 +130,24 @@ PLAN_CASES = [
     ("qft_random", lambda: C.qft_random_workload(15, 3, seed=8).gates, 15),
     ("mixed", lambda: C.pack(C.ghz(12) + [C.gate_swap(0, 11), C.gate_u(C.haar_u2(np.random.default_rng(1)), 11, (0, 3, 7))]
                              + C.random_layers(12, 2, np.random.default_rng(2))), 12),
+    ("two_qubit", lambda: C.pack(two_qubit_circuit(14, np.random.default_rng(9))), 14),
 ]
+
+
+def two_qubit_circuit(n, rng):
+    """Dense two-qubit gates on near and far qubit pairs (some controlled, one identity), mixed with one-qubit
+    gates, CNOTs and SWAPs."""
+    gates = []
+    for layer in range(3):
+        for q in range(0, n - 1, 2):
+            a, b = (q, q + 1) if layer % 2 == 0 else (q + 1, (q + 7) % n)
+            ctl = () if q % 4 else ((b + 2) % n,) if (b + 2) % n not in (a, b) else ()
+            gates.append(C.gate_u4(C.haar_u4(rng), a, b, ctl))
+        gates.append(C.gate_u(C.haar_u2(rng), layer))
+        gates.append(C.cnot(layer, n - 1 - layer))
+        gates.append(C.gate_swap(layer, n - 2))
+    gates.append(C.gate_u4(np.eye(4), 2, 9))
+    return gates
 
 
 @pytest.mark.parametrize("name,make,n", PLAN_CASES, ids=[c[0] for c in PLAN_CASES])
@@ -121,8 +159,13 @@ def test_planner_schedule_is_a_valid_reordering(lib, name, make, n, dtype, chunk
     order = plan["order_of_gate"]
     last = {}
     for i, g in enumerate(gates):
-        qs = [int(g["target"])] + ([int(g["target2"])] if g["kind"] == C.GATE_SWAP else
-                                   [int(c) for c in g["controls"][:g["ncontrols"]]])
+        kind = int(g["kind"])
+        if kind == C.GATE_U4_ROW:
+            assert order[i] == order[i - 1] + 1  # a two-qubit gate's records stay together
+            continue
+        qs = [int(g["target"])] + ([int(g["target2"])] if kind in (C.GATE_SWAP, C.GATE_U4) else [])
+        if kind != C.GATE_SWAP:
+            qs += [int(c) for c in g["controls"][:g["ncontrols"]]]
         for q in qs:
             if q in last:
                 assert order[i] > order[last[q]]
@@ -140,6 +183,18 @@ def test_planner_schedule_is_a_valid_reordering(lib, name, make, n, dtype, chunk
             a, b = int(g["target"]), int(g["target2"])
             perm[a], perm[b] = perm[b], perm[a]
             assert steps[i] == -1
+            continue
+        if g["kind"] == C.GATE_U4_ROW:
+            assert steps[i] == steps[i - 1]
+            continue
+        if g["kind"] == C.GATE_U4:
+            v = C.unpack_u4(gates[i:i + 4])
+            if np.array_equal(v, np.eye(4)):
+                assert steps[i] == -1
+                continue
+            assert steps[i] >= 0
+            for t in (int(g["target"]), int(g["target2"])):
+                assert plan["step_qmask"][steps[i]] >> np.uint64(perm[t]) & np.uint64(1)
             continue
         u = C.unpack_u(g)
         if np.array_equal(u, np.eye(2)):
