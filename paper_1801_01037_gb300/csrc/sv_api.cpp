@@ -110,6 +110,23 @@ int upload_plan(sv_state *s, const Plan &P, void **d_blob) {
 
 int f64_share_of(const sv_state *s) { return s->f64_share >= 0 ? s->f64_share : kDefaultF64Share; }
 
+int ensure_scratch(sv_state *s) {
+  cudaError_t e;
+  if (!s->d_scalars && (e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess) {
+    s->d_scalars = nullptr;
+    return cuda_fail(e, "state scratch allocation");
+  }
+  if (!s->d_sched && (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess) {
+    s->d_sched = nullptr;
+    return cuda_fail(e, "state scratch allocation");
+  }
+  if (!s->stage_ev && (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    s->stage_ev = nullptr;
+    return cuda_fail(e, "state scratch allocation");
+  }
+  return SV_OK;
+}
+
 int maybe_renormalize(sv_state *s, int applied) {
   if (s->renorm_period <= 0) return SV_OK;
   s->gates_since_renorm += applied;
@@ -323,14 +340,10 @@ int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_z
     cudaGetLastError();
     return set_error(SV_ERR_OOM, "cudaMalloc of the state failed");
   }
-  if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
-    cudaFree(s->psi);
-    if (s->d_scalars) cudaFree(s->d_scalars);
-    if (s->d_sched) cudaFree(s->d_sched);
-    delete s;
-    return cuda_fail(e, "state scratch allocation");
+  int rc = ensure_scratch(s);
+  if (rc != SV_OK) {
+    sv_destroy(s);
+    return rc;
   }
   if (init_zero) {
     if ((e = launch_init_basis(s->psi, n, mode_of(s), 0, st)) != cudaSuccess) {
@@ -378,14 +391,9 @@ sv_status sv_create_from_buffer(int n, sv_dtype dtype, void *dev_ptr, void *stre
   s->canonical = 1;
   s->perm.resize(n);
   for (int t = 0; t < n; ++t) s->perm[t] = t;
-  cudaError_t e;
-  if ((e = cudaMalloc(&s->d_scalars, sizeof(double) * (norm_parts() + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
-    if (s->d_scalars) cudaFree(s->d_scalars);
-    if (s->d_sched) cudaFree(s->d_sched);
-    delete s;
-    return cuda_fail(e, "state scratch allocation");
+  if ((rc = ensure_scratch(s)) != SV_OK) {
+    sv_destroy(s);
+    return rc;
   }
   *out = s;
   return SV_OK;
@@ -501,6 +509,8 @@ static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool 
     const int rc = validate_records(gates, ngates, s->n, why, bad);
     if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
   }
+  int src = ensure_scratch(s);
+  if (src != SV_OK) return src;
   std::vector<sv_gate> rest;
   const int prc = product_prologue(s, gates, ngates, rest);
   if (prc != SV_OK) return prc;

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -76,16 +77,48 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
     for (sv_state *s : states) if (s) sv_destroy(s);
     return code;
   };
-  size_t max_rounds = 0;
+  // One device allocation holds every state of the batch (256-byte aligned slices); each state keeps a
+  // reference, so the memory is freed when the last of them is destroyed.  Their small scratch buffers are
+  // made on first use.
+  std::vector<size_t> off(count);
+  size_t total = 0;
   for (int i = 0; i < count; ++i) {
-    if ((rc = alloc_state(n[i], dtype, st, &states[i], false)) != SV_OK) {
-      const std::string msg = sv_last_error();
-      cleanup(rc);
-      return set_error(rc, "circuit " + std::to_string(i) + ": " + msg);
-    }
-    plan_fresh(states[i], gates[i], ngates[i], plans[i]);
-    max_rounds = std::max(max_rounds, plans[i].passes.size());
+    off[i] = total;
+    total += ((amp_bytes(dtype) << n[i]) + 255) & ~(size_t)255;
   }
+  if (std::getenv("SV_FAULT_ALLOC")) return set_error(SV_ERR_OOM, "allocation failure injected (SV_FAULT_ALLOC)");
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+  if (total > free_b) return set_error(SV_ERR_OOM, "batch states of " + std::to_string(total) + " bytes exceed free device memory");
+  void *base = nullptr;
+  if ((e = cudaMalloc(&base, total)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(SV_ERR_OOM, "cudaMalloc of the batch states failed");
+  }
+  std::shared_ptr<void> arena(base, [](void *p) { cudaFree(p); });
+  for (int i = 0; i < count; ++i) {
+    sv_state *s = new sv_state();
+    s->n = n[i];
+    s->dtype = dtype;
+    s->stream = st;
+    s->perm.resize(n[i]);
+    for (int t = 0; t < n[i]; ++t) s->perm[t] = t;
+    s->psi = (char *)base + off[i];
+    s->owned = false;
+    s->arena = arena;
+    states[i] = s;
+  }
+  // Plans are independent: several host threads make them.
+  const int nthreads = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(16, (count + 31) / 32)));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&, t] {
+      for (int i = t; i < count; i += nthreads) plan_fresh(states[i], gates[i], ngates[i], plans[i]);
+    });
+  for (std::thread &th : pool) th.join();
+  size_t max_rounds = 0;
+  for (int i = 0; i < count; ++i) max_rounds = std::max(max_rounds, plans[i].passes.size());
   // Gates of every circuit in one device blob; per round, the pass descriptors and chunk prefix sums.
   std::vector<size_t> blob_off(count);
   size_t blob_bytes = 0;
@@ -127,7 +160,7 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
       plan_pass_pointers(plans[i], (int)r, (const unsigned char *)dg.p + blob_off[i], d);
       d.init_x = plans[i].passes[r].init_x;
     }
-  cudaError_t e = cudaMemcpyAsync(dg.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+  e = cudaMemcpyAsync(dg.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ds.p, starts.data(), starts.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   const int mode = default_mode(dtype);

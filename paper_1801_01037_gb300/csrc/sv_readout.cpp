@@ -140,6 +140,8 @@ sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const
 
 sv_status sv_norm(sv_state *s, double *out) {
   if (!s || !out) return set_error(SV_ERR_ARG, "NULL argument");
+  const int src = ensure_scratch(s);
+  if (src != SV_OK) return src;
   double *d_out = s->d_scalars + norm_parts();
   cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -153,6 +155,8 @@ sv_status sv_expect_z(sv_state *s, uint64_t mask, double *out) {
   uint64_t pmask = 0;  // the same qubits, as physical index bits
   for (int t = 0; t < s->n; ++t)
     if (mask >> t & 1ull) pmask |= 1ull << s->perm[t];
+  const int src = ensure_scratch(s);
+  if (src != SV_OK) return src;
   double *d_out = s->d_scalars + norm_parts();
   cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream, pmask);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -216,6 +220,8 @@ sv_status sv_sample(sv_state *s, const double *u, uint64_t count, uint64_t *out)
 sv_status sv_renormalize(sv_state *s) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
   s->product = false;
+  const int src = ensure_scratch(s);
+  if (src != SV_OK) return src;
   double *d_out = s->d_scalars + norm_parts();
   cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
   if (e == cudaSuccess) e = launch_scale(s->psi, s->n, mode_of(s), d_out, s->stream);
@@ -231,6 +237,8 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
     const int rc = validate_records(gates, ngates, s->n, why, bad);
     if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
   }
+  int src = ensure_scratch(s);
+  if (src != SV_OK) return src;
   std::vector<sv_gate> rest;
   const int prc = product_prologue(s, gates, ngates, rest);
   if (prc != SV_OK) return prc;

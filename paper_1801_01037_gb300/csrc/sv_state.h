@@ -1,6 +1,7 @@
 // Host-side state handle and helpers shared by the API, the batch runner and the server.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -24,6 +25,7 @@ struct sv_state {
   int arith = SV_ARITH_AUTO;
   void *psi = nullptr;
   bool owned = true;
+  std::shared_ptr<void> arena;  // batch states: the shared allocation psi points into (freed with the last one)
   cudaStream_t stream = nullptr;
   std::vector<int> perm;      // logical qubit -> physical bit
   int chunk_k = 0;            // 0 = default
@@ -81,6 +83,9 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st,
 int ensure_event_pool(sv_state *s, size_t steps);
 std::vector<int> step_kinds(const Plan &P);
 int canonicalize_now(sv_state *s);
+// Allocate the state's small scratch (norm partials, mixed-pass scheduler, staging event) if not done yet.
+// Must not run inside a stream capture.
+int ensure_scratch(sv_state *s);
 // Product-state start: fold leading single-qubit gates into the factors and re-form psi; (gates, ngates)
 // then name the remaining records, stored in `rest`.
 int product_prologue(sv_state *s, const sv_gate *&gates, size_t &ngates, std::vector<sv_gate> &rest);

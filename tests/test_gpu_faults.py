@@ -32,6 +32,23 @@ def test_injected_allocation_failure_is_reported_and_recoverable():
     B.sv_destroy(h)
 
 
+def test_injected_allocation_failure_of_a_batch():
+    """The batch's single state allocation fails as if out of memory: nothing is returned or leaked, and the
+    next batch runs."""
+    import circuits as C
+    ws = C.batched_workloads(6, n_lo=3, n_hi=9, d_lo=2, d_hi=4, seed=5)
+    os.environ["SV_FAULT_ALLOC"] = "1"
+    try:
+        with pytest.raises(B.SvError) as e:
+            B.sv_run_batch([w.n for w in ws], B.SV_C64, [w.gates for w in ws])
+        assert e.value.code == B.SV_ERR_OOM and "injected" in str(e.value)
+    finally:
+        del os.environ["SV_FAULT_ALLOC"]
+    handles = B.sv_run_batch([w.n for w in ws], B.SV_C64, [w.gates for w in ws])
+    for h in handles:
+        B.sv_destroy(h)
+
+
 def poll_until(srv, t, timeout_s=60.0):
     t0 = time.time()
     while time.time() - t0 < timeout_s:
