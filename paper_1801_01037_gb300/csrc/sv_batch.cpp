@@ -148,8 +148,8 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
     starts.push_back(R.total);
     rounds.push_back(R);
   }
-  DevBuf dg, dd, ds;
-  if (dg.ensure(blob.size(), st) != SV_OK ||
+  DevBuf dg, dd, ds, dsched;
+  if (dsched.ensure(sizeof(FusedSched), st) != SV_OK || dg.ensure(blob.size(), st) != SV_OK ||
       dd.ensure(std::max<size_t>(1, descs.size()) * sizeof(PassDesc), st) != SV_OK ||
       ds.ensure(std::max<size_t>(1, starts.size()) * sizeof(uint64_t), st) != SV_OK)
     return cleanup(set_error(SV_ERR_OOM, "batch descriptor allocation failed"));
@@ -167,7 +167,7 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
   for (size_t r = 0; r < rounds.size() && e == cudaSuccess; ++r) {
     const Round &R = rounds[r];
     e = launch_fused_batch((const PassDesc *)dd.p + R.desc_off, (const uint64_t *)ds.p + R.start_off, R.npass, R.total,
-                           mode, R.kmax, st);
+                           mode, R.kmax, st, kDefaultF64Share, (FusedSched *)dsched.p);
   }
   // The descriptor buffers are freed on return, so wait for the launches that read them.
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -212,7 +212,7 @@ struct sv_server {
   bool stop = false;
   std::thread th;
   cudaStream_t stream = nullptr;
-  DevBuf d_desc, d_start;
+  DevBuf d_desc, d_start, d_sched;
   PassDesc *h_desc = nullptr;
   uint64_t *h_start = nullptr;
   size_t h_cap = 0;
@@ -288,7 +288,8 @@ struct sv_server {
       const size_t m = active.size();
       const size_t used_m = in_round.size();
       if (ensure_host(used_m) != SV_OK || d_desc.ensure(used_m * sizeof(PassDesc), stream) != SV_OK ||
-          d_start.ensure((used_m + 1) * sizeof(uint64_t), stream) != SV_OK) {
+          d_start.ensure((used_m + 1) * sizeof(uint64_t), stream) != SV_OK ||
+          d_sched.ensure(sizeof(FusedSched), stream) != SV_OK) {
         for (Active &a : active) {
           fail_request(a.ticket, SV_ERR_OOM, "round descriptor allocation failed");
           if (a.d_gates) cudaFree(a.d_gates);
@@ -316,7 +317,8 @@ struct sv_server {
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_start.p, h_start, (used_m + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, stream);
       if (e == cudaSuccess)
-        e = launch_fused_batch((const PassDesc *)d_desc.p, (const uint64_t *)d_start.p, (int)used_m, total, mode, kmax, stream);
+        e = launch_fused_batch((const PassDesc *)d_desc.p, (const uint64_t *)d_start.p, (int)used_m, total, mode, kmax, stream,
+                               kDefaultF64Share, (FusedSched *)d_sched.p);
       if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
       lk.lock();
       std::vector<Active> keep;

@@ -390,6 +390,46 @@ __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused_bat
   }
 }
 
+// Batched pass with the FP64 / double-float split of k_fused_mixed: the round's chunks are numbered in order
+// of their passes, chunk c runs in FP64 iff c mod 100 < share, and each role draws from its own counter.
+__device__ __forceinline__ int batch_pass_of(const uint64_t *chunk_start, int npass, uint64_t b) {
+  int lo = 0, hi = npass - 1;  // last pass with chunk_start <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (chunk_start[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
+    k_fused_batch_mixed(const PassDesc *__restrict__ passes, const uint64_t *__restrict__ chunk_start, int npass,
+                        uint64_t total, int kmax, int share, FusedSched *sched) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int role;
+  __shared__ unsigned long long next;
+  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)16 << kmax));
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    role = atomicAdd(&sched->sm_slot[smid % kSchedSlots], 1u) == 0u ? 1 : 0;
+  }
+  __syncthreads();
+  const uint64_t rest = (uint64_t)(100 - share);
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(&sched->next[role], 1ull);
+    __syncthreads();
+    const uint64_t j = next;
+    __syncthreads();
+    const uint64_t c = role ? (j / (uint64_t)share) * 100ull + (j % (uint64_t)share)
+                            : (j / rest) * 100ull + (uint64_t)share + (j % rest);
+    if (c >= total) break;
+    const int pi = batch_pass_of(chunk_start, npass, c);
+    const PassDesc p = passes[pi];
+    if (role) fused_chunk<MODE_C128_F64>(p, c - chunk_start[pi], (double2 *)smraw, rowoff);
+    else fused_chunk<MODE_C128_DF32>(p, c - chunk_start[pi], (float4 *)smraw, rowoff);
+  }
+}
+
 // Largest dynamic shared-memory size already granted to kernel `fn` on the current device; raises it if
 // `bytes` is larger.  One slot per (kernel, device).
 cudaError_t ensure_smem(const void *fn, int bytes, int *granted_per_device) {
@@ -485,8 +525,24 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
 }
 
 cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
-                               int mode, int kmax, cudaStream_t st) {
+                               int mode, int kmax, cudaStream_t st, int f64_share, FusedSched *sched) {
   if (total == 0 || npass == 0) return cudaSuccess;
+  if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
+    const int smem = smem_bytes<MODE_C128_DF32>(kmax);
+    static int granted[64] = {0};
+    cudaError_t e = ensure_smem((const void *)k_fused_batch_mixed, smem, granted);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_batch_mixed, kFusedThreads, smem);
+    if (occ < 1) occ = 1;
+    const uint64_t grid = (uint64_t)sms() * occ;
+    if (occ >= 2 && total >= 4 * grid) {
+      if ((e = cudaMemsetAsync(sched, 0, sizeof(FusedSched), st)) != cudaSuccess) return e;
+      k_fused_batch_mixed<<<(unsigned)grid, kFusedThreads, smem, st>>>(d_passes, d_chunk_start, npass, total, kmax,
+                                                                        f64_share, sched);
+      return cudaGetLastError();
+    }
+  }
   switch (mode) {
     case MODE_C64_F32: return fused_batch_launch<MODE_C64_F32>(d_passes, d_chunk_start, npass, total, kmax, st);
     case MODE_C128_F64: return fused_batch_launch<MODE_C128_F64>(d_passes, d_chunk_start, npass, total, kmax, st);

@@ -117,7 +117,10 @@ cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cuda
 // Batched fused pass: `npass` pass descriptors in device memory; block b handles chunk b - chunk_start[p]
 // of pass p, where chunk_start is an exclusive prefix sum over the passes' chunk counts (device array of
 // npass + 1 entries).  All passes share `mode`; each has its own k <= kmax (shared memory is sized for kmax).
+// f64_share / sched: as for launch_fused (complex128 double-float: that percent of the round's chunks, by
+// their index in the round, run in native FP64 on one CTA per SM).
 cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass,
-                               uint64_t total_chunks, int mode, int kmax, cudaStream_t st);
+                               uint64_t total_chunks, int mode, int kmax, cudaStream_t st, int f64_share = 0,
+                               FusedSched *sched = nullptr);
 
 } // namespace svi
