@@ -569,6 +569,48 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
     return !needs_pairing(cls) || inQ[perm[gates[i].target]];
   };
 
+  // Gates a pass over the chunk bits inQ plus `extra` would apply from the current frontier, counted on
+  // copies of the scheduling state (SWAP relabels included).
+  auto closure_with = [&](const bool *inQ, int extra) {
+    bool q2[64];
+    for (int x = 0; x < n; ++x) q2[x] = inQ[x];
+    q2[extra] = true;
+    std::vector<size_t> h = head;
+    std::vector<int> pm = perm;
+    std::set<int> rd = ready;
+    auto ready_in = [&](int i) {
+      int qs[8];
+      const int m = qubits_of(i, qs);
+      for (int j = 0; j < m; ++j)
+        if (h[qs[j]] >= q[qs[j]].size() || q[qs[j]][h[qs[j]]] != i) return false;
+      return true;
+    };
+    auto fits_in = [&](int i) {
+      const int cls = cls_of[i];
+      if (cls < 0) return true;
+      if (cls == GC_DENSE4) return q2[pm[gates[i].target]] && q2[pm[gates[i].target2]];
+      return !needs_pairing(cls) || q2[pm[gates[i].target]];
+    };
+    int run = 0;
+    for (;;) {
+      int ch = -1;
+      for (int i : rd)
+        if (fits_in(i)) { ch = i; break; }
+      if (ch < 0) break;
+      if (cls_of[ch] == -2) std::swap(pm[gates[ch].target], pm[gates[ch].target2]);
+      else if (cls_of[ch] >= 0) ++run;
+      rd.erase(ch);
+      int qs[8];
+      const int m = qubits_of(ch, qs);
+      for (int j = 0; j < m; ++j) ++h[qs[j]];
+      for (int j = 0; j < m; ++j) {
+        const int u = qs[j];
+        if (h[u] < q[u].size() && ready_in(q[u][h[u]])) rd.insert(q[u][h[u]]);
+      }
+    }
+    return run;
+  };
+
   bool first_pass = true;
   while (!ready.empty() || (first_pass && cfg.init_first)) {
     bool inQ[64] = {false};
@@ -597,7 +639,7 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
         continue;
       }
       if (qcount >= k || ready.empty()) break;
-      // Add the physical bit that the most ready gates are waiting for (ties: the earliest gate).
+      // Add the physical bit that the most ready gates are waiting for (ties: the earliest gate) ...
       int best_bit = -1, best_count = 0;
       int counts[64] = {0};
       for (int i : ready) {
@@ -606,6 +648,16 @@ void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_ga
           if (b >= 0 && !inQ[b] && ++counts[b] > best_count) { best_count = counts[b]; best_bit = b; }
       }
       if (best_bit < 0) break;
+      // ... unless another bit lets more gates run in this pass: for every candidate bit, simulate the rest
+      // of the pass (the gates that become ready as others run included) and take the largest count.
+      if (cfg.lookahead) {
+        int best_run = closure_with(inQ, best_bit);
+        for (int b = 0; b < n; ++b) {
+          if (inQ[b] || b == best_bit) continue;
+          const int run = closure_with(inQ, b);
+          if (run > best_run) { best_run = run; best_bit = b; }
+        }
+      }
       inQ[best_bit] = true;
       ++qcount;
     }

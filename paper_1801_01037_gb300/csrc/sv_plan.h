@@ -16,6 +16,7 @@ struct PlanConfig {
   bool single_as_sweep = true;  // a pass holding one gate is emitted as a sweep instead
   bool init_first = false;  // the first pass starts from |init_x> (batched / served states)
   bool cubes = false;       // group each pass's gates into register cubes (complex64 passes, k >= 8)
+  bool lookahead = true;    // grow a pass's chunk bits by simulated gate count (false: by immediate demand)
   uint64_t init_x = 0;
 };
 
