@@ -102,92 +102,113 @@ __device__ __noinline__ void chunk_quads(typename Arith<MODE>::S *sm, const DevG
 
 // ---- Complex64 register cubes (GC_CUBE) ----------------------------------------------------------------
 // v[s] holds the amplitude whose cube bits spell s (bit i of s = chunk bit pos[i]).  Each routine applies one
-// gate to the 16 registers with the same arithmetic, in the same order, as the shared-memory pair loop, so
-// the two paths give identical results.  cs: the gate's control bits inside the cube, as cube bits.
+// gate to the 2^CB registers with the same arithmetic, in the same order, as the shared-memory pair loop, so
+// the two paths give identical results.  cs: the gate's control bits inside the cube, as cube bits (the
+// planner stores it, and the cube slot of the target, in the gate record; see GC_CUBE).
 using C64 = Arith<MODE_C64_F32>;
 
-template <int J, int CLS, bool CTL>
-__device__ __forceinline__ void cube_pairs(float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
+template <int CB, int J, int CLS, bool CTL>
+__device__ __forceinline__ void cube_pairs(float2 (&v)[1 << CB], const CoefF32 &cf, uint32_t cs) {
+  if constexpr (J < CB) {
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
-    if (s & (1 << J)) continue;
-    if (CTL && ((uint32_t)s & cs) != cs) continue;
-    apply_pair<MODE_C64_F32>(CLS, cf, v[s], v[s | (1 << J)]);
+    for (int s = 0; s < (1 << CB); ++s) {
+      if (s & (1 << J)) continue;
+      if (CTL && ((uint32_t)s & cs) != cs) continue;
+      apply_pair<MODE_C64_F32>(CLS, cf, v[s], v[s | (1 << J)]);
+    }
   }
 }
 
 // CTL = false: the gate has no control bit inside the cube (cs = 0), so no per-pair test is compiled.
-template <int CLS, bool CTL = true>
-__device__ __forceinline__ void cube_pairs_at(int j, float2 (&v)[16], const CoefF32 &cf, uint32_t cs) {
+template <int CB, int CLS, bool CTL = true>
+__device__ __forceinline__ void cube_pairs_at(int j, float2 (&v)[1 << CB], const CoefF32 &cf, uint32_t cs) {
   switch (j) {
-    case 0: cube_pairs<0, CLS, CTL>(v, cf, cs); break;
-    case 1: cube_pairs<1, CLS, CTL>(v, cf, cs); break;
-    case 2: cube_pairs<2, CLS, CTL>(v, cf, cs); break;
-    default: cube_pairs<3, CLS, CTL>(v, cf, cs); break;
+    case 0: cube_pairs<CB, 0, CLS, CTL>(v, cf, cs); break;
+    case 1: cube_pairs<CB, 1, CLS, CTL>(v, cf, cs); break;
+    case 2: cube_pairs<CB, 2, CLS, CTL>(v, cf, cs); break;
+    case 3: cube_pairs<CB, 3, CLS, CTL>(v, cf, cs); break;
+    default: cube_pairs<CB, 4, CLS, CTL>(v, cf, cs); break;
   }
 }
 
-// Diagonal gate whose target bit is the same for all 16 registers (one = that bit).
-__device__ __forceinline__ void cube_diag_uniform(float2 (&v)[16], const CoefF32 &cf, uint32_t cs, bool one,
+// Diagonal gate whose target bit is the same for all registers (one = that bit).
+template <int CB>
+__device__ __forceinline__ void cube_diag_uniform(float2 (&v)[1 << CB], const CoefF32 &cf, uint32_t cs, bool one,
                                                   bool phase) {
   if (!one && phase) return;
-  const int e = one ? 3 : 0;
-  const float qr = e ? cf.q[6] : cf.q[0], qi = e ? cf.q[7] : cf.q[1];
+  const float qr = one ? cf.q[6] : cf.q[0], qi = one ? cf.q[7] : cf.q[1];
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
+  for (int s = 0; s < (1 << CB); ++s) {
     if (((uint32_t)s & cs) != cs) continue;
     v[s] = make_float2(__fmaf_rn(qr, v[s].x, -qi * v[s].y), __fmaf_rn(qr, v[s].y, qi * v[s].x));
   }
 }
 
-__device__ __forceinline__ uint32_t cube_off(int s, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
-  return ((s & 1) ? m0 : 0u) | ((s & 2) ? m1 : 0u) | ((s & 4) ? m2 : 0u) | ((s & 8) ? m3 : 0u);
+// The slot map is linear over GF(2) (an XOR of shifted index bits), so the slot of base | (cube bits of s) is
+// slot(base) XOR the slots of the cube bits set in s.
+template <int CB>
+__device__ __forceinline__ uint32_t cube_xoff(int s, const uint32_t (&soff)[CB]) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int j = 0; j < CB; ++j)
+    if (s & (1 << j)) x ^= soff[j];
+  return x;
 }
 
-// The cube's `cnt` gates over chunk bits packed in `pos`, for every base index of the chunk.
-__device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint32_t pos, uint64_t base, float2 *sm, int k) {
-  const int p0 = pos & 0xff, p1 = (pos >> 8) & 0xff, p2 = (pos >> 16) & 0xff, p3 = (pos >> 24) & 0xff;
-  const uint32_t m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2, m3 = 1u << p3;
-  const uint32_t cube = m0 | m1 | m2 | m3;
-  const uint32_t nbase = 1u << (k - kCubeBits);
-  for (uint32_t bi = threadIdx.x; bi < nbase; bi += kFusedThreads) {
-    const uint32_t bidx = ins0(ins0(ins0(ins0(bi, p0), p1), p2), p3);
-    float2 v[16];
+// The cube's `cnt` gates over the CB chunk bits packed in `posw` (one byte each, ascending), for every base
+// index of the chunk.
+template <int CB>
+__device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint64_t posw, uint64_t base, float2 *sm, int k) {
+  int p[CB];
+  uint32_t soff[CB], cube = 0;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = sm[slot<MODE_C64_F32>(bidx | cube_off(s, m0, m1, m2, m3))];
+  for (int j = 0; j < CB; ++j) {
+    p[j] = (int)((posw >> (8 * j)) & 0xffu);
+    cube |= 1u << p[j];
+    soff[j] = slot<MODE_C64_F32>(1u << p[j]);
+  }
+  const uint32_t nbase = 1u << (k - CB);
+  for (uint32_t bi = threadIdx.x; bi < nbase; bi += kFusedThreads) {
+    uint32_t bidx = bi;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) bidx = ins0(bidx, p[j]);
+    const uint32_t b0 = slot<MODE_C64_F32>(bidx);
+    float2 v[1 << CB];
+#pragma unroll
+    for (int s = 0; s < (1 << CB); ++s) v[s] = sm[b0 ^ cube_xoff<CB>(s, soff)];
     for (int gi = 0; gi < cnt; ++gi) {
       const DevGate &g = gs[gi];
       if ((base & g.gmask) != g.gmask) continue;
-      const uint32_t cm = (uint32_t)g.cmask, cb = cm & ~cube;
+      const uint64_t cmw = g.cmask;
+      const uint32_t cb = (uint32_t)cmw & ~cube;
       if ((bidx & cb) != cb) continue;
-      const uint32_t cs = ((cm >> p0) & 1u) | (((cm >> p1) & 1u) << 1) | (((cm >> p2) & 1u) << 2) |
-                          (((cm >> p3) & 1u) << 3);
+      const uint32_t cs = (uint32_t)(cmw >> 32) & 31u;
+      const int j = (int)((cmw >> 40) & 7u) - 1;
       const uint32_t cls = g.cls;
-      const int t = g.target;
-      const int j = t == p0 ? 0 : t == p1 ? 1 : t == p2 ? 2 : t == p3 ? 3 : -1;
       CoefF32 cf;
-      if (cls != GC_X) {
-        // The complex64 coefficients: two 16-byte loads (DevGate records are 192 bytes, 16-byte aligned).
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(g.qh)), b = __ldg(reinterpret_cast<const float4 *>(g.qh) + 1);
-        cf.q[0] = a.x; cf.q[1] = a.y; cf.q[2] = a.z; cf.q[3] = a.w;
-        cf.q[4] = b.x; cf.q[5] = b.y; cf.q[6] = b.z; cf.q[7] = b.w;
-      }
+      if (cls != GC_X) C64::coef(cf, g);
       switch (cls) {
         case GC_GENERAL:
-          if (cs == 0) cube_pairs_at<GC_GENERAL, false>(j, v, cf, cs);
-          else cube_pairs_at<GC_GENERAL>(j, v, cf, cs);
+          if (cs == 0) cube_pairs_at<CB, GC_GENERAL, false>(j, v, cf, cs);
+          else cube_pairs_at<CB, GC_GENERAL>(j, v, cf, cs);
           break;
-        case GC_ANTIDIAG: cube_pairs_at<GC_ANTIDIAG>(j, v, cf, cs); break;
-        case GC_X: cube_pairs_at<GC_X>(j, v, cf, cs); break;
-        default:
-          if (j >= 0 && cls == GC_DIAG) cube_pairs_at<GC_DIAG>(j, v, cf, cs);
-          else if (j >= 0) cube_pairs_at<GC_PHASE>(j, v, cf, cs);
-          else cube_diag_uniform(v, cf, cs, t >= 0 ? ((bidx >> t) & 1u) != 0 : (base & g.tmask) != 0, cls == GC_PHASE);
+        case GC_ANTIDIAG: cube_pairs_at<CB, GC_ANTIDIAG>(j, v, cf, cs); break;
+        case GC_X: cube_pairs_at<CB, GC_X>(j, v, cf, cs); break;
+        default: {
+          const int t = g.target;
+          if (j >= 0 && cls == GC_DIAG) cube_pairs_at<CB, GC_DIAG>(j, v, cf, cs);
+          else if (j >= 0) cube_pairs_at<CB, GC_PHASE>(j, v, cf, cs);
+          else cube_diag_uniform<CB>(v, cf, cs, t >= 0 ? ((bidx >> t) & 1u) != 0 : (base & g.tmask) != 0, cls == GC_PHASE);
           break;
+        }
       }
     }
+    // Recompute the slots for the store (an opaque copy of b0 keeps the compiler from holding all 2^CB
+    // load addresses live across the gates).
+    uint32_t b1 = b0;
+    asm volatile("" : "+r"(b1));
 #pragma unroll
-    for (int s = 0; s < 16; ++s) sm[slot<MODE_C64_F32>(bidx | cube_off(s, m0, m1, m2, m3))] = v[s];
+    for (int s = 0; s < (1 << CB); ++s) sm[b1 ^ cube_xoff<CB>(s, soff)] = v[s];
   }
 }
 
@@ -265,7 +286,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     }
     if (cls == GC_CUBE) {
       if constexpr (MODE == MODE_C64_F32) {
-        cube_run(p.gates + gi + 1, g.target, (uint32_t)g.cmask, base, sm, k);
+        cube_run<kCubeBits>(p.gates + gi + 1, g.target, g.cmask, base, sm, k);
         gi += g.target;
         __syncthreads();
       }

@@ -30,10 +30,12 @@ enum GateClass : uint32_t {
 };
 
 // Register cube.  Inside a complex64 fused pass, a header DevGate with cls = GC_CUBE says that the next
-// `target` gates act only on the four chunk-local bits packed in the low four bytes of `cmask` (ascending),
-// apart from diagonal gates, which may sit on any bit.  Each thread then holds the 16 amplitudes that
-// differ in those four bits in registers and applies all of the cube's gates there: one shared-memory
-// round trip for the run instead of one per gate.
+// `target` gates act only on the `tmask` (= kCubeBits) chunk-local bits packed one per byte in `cmask`
+// (ascending), apart from diagonal gates, which may sit on any bit.  Each thread then holds the 2^kCubeBits
+// amplitudes that differ in those bits in registers and applies all of the cube's gates there: one
+// shared-memory round trip for the run instead of one per gate.  The gates of a cube carry their in-cube
+// control bits and target slot in the upper half of `cmask` (see group_cubes).  Five bits (32 registers
+// of data per thread) measured the same speed and spilled at the 128-register cap.
 constexpr int kCubeBits = 4;
 
 // One gate as the kernels see it.  In a single-gate sweep, `target` and `cmask` are physical bits.  Inside

@@ -309,10 +309,12 @@ DevGate to_sweep_gate(const sv_gate &g, const Sched &s) {
 
 // Split a pass's gate run (chunk-local targets) into register cubes, in order: a cube takes gates while the
 // distinct targets of its pairing gates stay within kCubeBits bits; diagonal gates join any cube; a two-qubit
-// gate ends the cube and is left outside any cube.  Unused
-// cube bits are filled from the top of the chunk, which keeps the threads of a half-warp on distinct
-// shared-memory banks for most bit sets.
+// gate ends the cube and is left outside any cube.  Unused cube bits are filled from the top of the chunk, which keeps the
+// threads of a half-warp on distinct shared-memory banks for most bit sets.  Each gate in a cube gets its
+// control bits inside the cube (as cube bits) in bits 32..36 of cmask and 1 + the cube slot of its target
+// (0: not in the cube) in bits 40..42, so the kernel does no per-gate bit search.
 void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out) {
+  const int cb = kCubeBits;
   size_t i = 0;
   while (i < run.size()) {
     if (run[i].cls == GC_DENSE4) {  // two-qubit gates run on their own, from shared memory (4 records)
@@ -329,21 +331,33 @@ void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &o
       if (!needs_pairing((int)g.cls) || g.target < 0) continue;
       const uint32_t tb = 1u << g.target;
       if (bits & tb) continue;
-      if (nb == kCubeBits) break;
+      if (nb == cb) break;
       bits |= tb;
       ++nb;
     }
-    for (int b = k - 1; b >= 0 && nb < kCubeBits; --b)
+    for (int b = k - 1; b >= 0 && nb < cb; --b)
       if (!(bits >> b & 1u)) { bits |= 1u << b; ++nb; }
+    int pos[8], np = 0;
+    for (int b = 0; b < k; ++b)
+      if (bits >> b & 1u) pos[np++] = b;
     DevGate h;
     std::memset(&h, 0, sizeof h);
     h.cls = GC_CUBE;
     h.target = (int32_t)(j - i);
-    int s = 0;
-    for (int b = 0; b < k; ++b)
-      if (bits >> b & 1u) h.cmask |= (uint64_t)b << (8 * s++);
+    h.tmask = (uint64_t)cb;
+    for (int s = 0; s < np; ++s) h.cmask |= (uint64_t)pos[s] << (8 * s);
     out.push_back(h);
-    out.insert(out.end(), run.begin() + i, run.begin() + j);
+    for (size_t x = i; x < j; ++x) {
+      DevGate g = run[x];
+      const uint32_t cm = (uint32_t)g.cmask;
+      uint64_t cs = 0, slot1 = 0;
+      for (int s = 0; s < np; ++s) {
+        if (cm >> pos[s] & 1u) cs |= 1ull << s;
+        if (g.target == pos[s]) slot1 = (uint64_t)(s + 1);
+      }
+      g.cmask = (uint64_t)cm | (cs << 32) | (slot1 << 40);
+      out.push_back(g);
+    }
     i = j;
   }
 }
