@@ -349,7 +349,8 @@ cudaError_t launch_init_basis(void *psi, int n, int mode, uint64_t x, cudaStream
 // Product state (Sec. V): amplitude k = prod_t g_t[bit t of k] with g_t = M_t f_t.  Table entry i < 2^h
 // holds the product over qubits 0..h-1 for low index bits i, entry 2^h + j the product over qubits h..n-1 for
 // high index bits j (FP64, qubits in ascending order).
-__global__ void k_product_tables(const double *__restrict__ fm, int n, int h, double2 *__restrict__ tab) {
+template <typename T>
+__global__ void k_product_tables(const double *__restrict__ fm, int n, int h, T *__restrict__ tab) {
   const uint64_t nlo = 1ull << h, total = nlo + (1ull << (n - h));
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
     const bool lo = i < nlo;
@@ -365,23 +366,19 @@ __global__ void k_product_tables(const double *__restrict__ fm, int n, int h, do
       re = nr;
       im = ni;
     }
-    tab[i] = make_double2(re, im);
+    tab[i] = T{(decltype(T::x))re, (decltype(T::x))im};  // complex64 tables are rounded once, here
   }
 }
 
+// One complex product per amplitude, in the state's precision (complex64: FP32 products of the rounded
+// tables, relative error a few 2^-24).
 template <typename G>
-__global__ void k_init_product(G *__restrict__ psi, int n, int h, const double2 *__restrict__ tab) {
+__global__ void k_init_product(G *__restrict__ psi, int n, int h, const G *__restrict__ tab) {
   const uint64_t N = 1ull << n, mlo = (1ull << h) - 1ull;
-  const double2 *hi = tab + (1ull << h);
+  const G *hi = tab + (1ull << h);
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < N; k += (uint64_t)gridDim.x * blockDim.x) {
-    const double2 a = tab[k & mlo], b = hi[k >> h];
-    if constexpr (sizeof(G) == 16) {
-      psi[k] = G{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-    } else {
-      // complex64: the tables rounded to float, one FP32 complex product (relative error a few 2^-24)
-      const float ar = (float)a.x, ai = (float)a.y, br = (float)b.x, bi = (float)b.y;
-      psi[k] = G{ar * br - ai * bi, ar * bi + ai * br};
-    }
+    const G a = tab[k & mlo], b = hi[k >> h];
+    psi[k] = G{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
   }
 }
 
@@ -390,12 +387,14 @@ uint64_t product_table_entries(int n) { return (1ull << (n / 2)) + (1ull << (n -
 cudaError_t launch_init_product(void *psi, int n, int mode, const double *d_fm, void *d_tab, cudaStream_t st) {
   const int h = n / 2;
   const uint64_t entries = product_table_entries(n);
-  k_product_tables<<<grid_for(entries, 256), 256, 0, st>>>(d_fm, n, h, (double2 *)d_tab);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const unsigned grid = grid_for(1ull << n, 256);
-  if (mode == MODE_C64_F32) k_init_product<float2><<<grid, 256, 0, st>>>((float2 *)psi, n, h, (const double2 *)d_tab);
-  else k_init_product<double2><<<grid, 256, 0, st>>>((double2 *)psi, n, h, (const double2 *)d_tab);
+  const unsigned tgrid = grid_for(entries, 256), grid = grid_for(1ull << n, 256);
+  if (mode == MODE_C64_F32) {
+    k_product_tables<float2><<<tgrid, 256, 0, st>>>(d_fm, n, h, (float2 *)d_tab);
+    k_init_product<float2><<<grid, 256, 0, st>>>((float2 *)psi, n, h, (const float2 *)d_tab);
+  } else {
+    k_product_tables<double2><<<tgrid, 256, 0, st>>>(d_fm, n, h, (double2 *)d_tab);
+    k_init_product<double2><<<grid, 256, 0, st>>>((double2 *)psi, n, h, (const double2 *)d_tab);
+  }
   return cudaGetLastError();
 }
 
