@@ -372,7 +372,83 @@ static bool is_identity4(const sv_gate *g) {
   return true;
 }
 
+static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates,
+                              size_t ngates, Plan &P);
+
+// Runs of uncontrolled one-qubit gates on one qubit, with no other record touching that qubit between them,
+// become one gate whose matrix is their product, composed in FP64 on the host (later x earlier).  `groups[j]`
+// lists the source records of reduced record j, in source order.  Returns the number of gates merged away.
+static size_t merge_one_qubit_runs(int n, const sv_gate *gates, size_t ngates, std::vector<sv_gate> &red,
+                                   std::vector<std::vector<int>> &groups) {
+  std::vector<int> open(n, -1);  // reduced record holding the qubit's open run, or -1
+  size_t merged = 0;
+  for (size_t i = 0; i < ngates; ++i) {
+    const sv_gate &g = gates[i];
+    if (g.kind == SV_GATE_U && g.ncontrols == 0 && open[g.target] >= 0) {
+      sv_gate &m = red[open[g.target]];
+      double r[8];
+      for (int row = 0; row < 2; ++row)
+        for (int col = 0; col < 2; ++col) {
+          double re = 0.0, im = 0.0;
+          for (int j = 0; j < 2; ++j) {
+            const double ur = g.U[4 * row + 2 * j], ui = g.U[4 * row + 2 * j + 1];
+            const double mr = m.U[4 * j + 2 * col], mi = m.U[4 * j + 2 * col + 1];
+            re += ur * mr - ui * mi;
+            im += ur * mi + ui * mr;
+          }
+          r[4 * row + 2 * col] = re;
+          r[4 * row + 2 * col + 1] = im;
+        }
+      std::memcpy(m.U, r, sizeof r);
+      groups[open[g.target]].push_back((int)i);
+      ++merged;
+      continue;
+    }
+    const int recs = g.kind == SV_GATE_U4 ? 4 : 1;
+    // every qubit this record touches closes its open run
+    open[g.target] = -1;
+    if (g.kind == SV_GATE_SWAP || g.kind == SV_GATE_U4) open[g.target2] = -1;
+    if (g.kind != SV_GATE_SWAP)
+      for (int c = 0; c < g.ncontrols; ++c) open[g.controls[c]] = -1;
+    for (int r = 0; r < recs; ++r) {
+      red.push_back(gates[i + r]);
+      groups.push_back({(int)(i + r)});
+    }
+    if (g.kind == SV_GATE_U && g.ncontrols == 0) open[g.target] = (int)red.size() - 1;
+    i += recs - 1;
+  }
+  return merged;
+}
+
 void make_plan(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates, size_t ngates, Plan &P) {
+  std::vector<sv_gate> red;
+  std::vector<std::vector<int>> groups;
+  red.reserve(ngates);
+  groups.reserve(ngates);
+  const size_t merged = cfg.merge ? merge_one_qubit_runs(n, gates, ngates, red, groups) : 0;
+  if (merged == 0) {
+    make_plan_records(n, cfg, perm, gates, ngates, P);
+    return;
+  }
+  make_plan_records(n, cfg, perm, red.data(), red.size(), P);
+  // Map the schedule record back to the source records: merged records share their step and take
+  // consecutive positions in the execution order.
+  std::vector<int> by_order(red.size());
+  for (size_t j = 0; j < red.size(); ++j) by_order[P.gate_order[j]] = (int)j;
+  std::vector<int> step(ngates, -1), ord(ngates, -1);
+  int o = 0;
+  for (int j : by_order)
+    for (int src : groups[j]) {
+      step[src] = P.gate_step[j];
+      ord[src] = o++;
+    }
+  P.gate_step.swap(step);
+  P.gate_order.swap(ord);
+  P.n_merged = (int)merged;
+}
+
+static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &perm, const sv_gate *gates,
+                              size_t ngates, Plan &P) {
   P = Plan();
   P.gate_step.assign(ngates, -1);
   P.gate_order.assign(ngates, -1);

@@ -17,6 +17,7 @@ struct PlanConfig {
   bool init_first = false;  // the first pass starts from |init_x> (batched / served states)
   bool cubes = false;       // group each pass's gates into register cubes (complex64 passes, k >= 8)
   bool lookahead = true;    // grow a pass's chunk bits by simulated gate count (false: by immediate demand)
+  bool merge = true;        // compose runs of one-qubit gates on one qubit into one matrix (FP64, host)
   uint64_t init_x = 0;
 };
 
@@ -33,7 +34,7 @@ struct Plan {
   std::vector<int> pass_gate_offset; // first DevGate of each pass in fused_gates
   std::vector<DevGate> fused_gates;
   std::vector<DevGate> sweep_gates;
-  int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_remaps = 0, n_skipped = 0;
+  int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_remaps = 0, n_skipped = 0, n_merged = 0;
   // Schedule record per source gate: the step that applies it (-1: folded into the layout or skipped) and
   // its position in execution order; per step the physical bits its chunks span (a sweep: its target bit).
   std::vector<int> gate_step, gate_order;

@@ -210,6 +210,40 @@ def test_planner_schedule_is_a_valid_reordering(lib, name, make, n, dtype, chunk
     assert seq == sorted(seq)
 
 
+def rotation_runs_circuit(n, rng):
+    """Runs of one-qubit rotations on each qubit (Rz Ry Rz) between CNOT layers, then an X X pair and an
+    S S^dagger pair (exact identities) after the last CNOT layer."""
+    gates = []
+    for layer in range(3):
+        for q in range(n):
+            gates += [C.gate_u(C.rz(rng.uniform(0, 6.3)), q), C.gate_u(C.ry(rng.uniform(0, 6.3)), q),
+                      C.gate_u(C.rz(rng.uniform(0, 6.3)), q)]
+        for q in range(0, n - 1, 2):
+            gates.append(C.cnot(q, q + 1) if layer % 2 == 0 else C.cnot(q + 1, (q + 2) % n))
+    gates += [C.gate_u(C.X, 0), C.gate_u(C.X, 0), C.gate_u(C.S, 3), C.gate_u(C.S.conj().T, 3)]
+    return C.pack(gates)
+
+
+@pytest.mark.parametrize("dtype", [B.SV_C128, B.SV_C64])
+def test_one_qubit_runs_are_composed(lib, dtype):
+    """Runs of one-qubit gates on one qubit become one gate (their product, FP64): the schedule keeps the
+    circuit's meaning (replayed through the oracle in plan order) and launches fewer gate applications."""
+    n = 14
+    gates = rotation_runs_circuit(n, np.random.default_rng(12))
+    plan = B.sv_plan_dry_run(n, dtype, gates)
+    order = plan["order_of_gate"]
+    assert sorted(order) == list(range(len(gates)))
+    want = oracle.simulate(n, gates, 5)
+    got = oracle.simulate(n, replay_in_plan_order(n, gates, plan), 5)
+    assert np.max(np.abs(got - want)) < 1e-12
+    steps = plan["step_of_gate"]
+    # the three rotations of a run share one step; X X and S S^dagger compose to the identity and are dropped
+    for i in range(0, 3 * n, 3):
+        assert steps[i] == steps[i + 1] == steps[i + 2] >= 0
+        assert order[i + 1] == order[i] + 1 and order[i + 2] == order[i] + 2
+    assert all(steps[len(gates) - 4 + j] == -1 for j in range(4))
+
+
 def test_fusion_reduces_launches(lib):
     w = C.random_workload(30, 20, seed=1002)
     plan = B.sv_plan_dry_run(30, B.SV_C128, w.gates)

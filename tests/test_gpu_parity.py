@@ -212,6 +212,30 @@ def test_buffer_state_over_torch_tensor_stays_in_logical_order():
         B.sv_destroy(h)
 
 
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n", [3, 14, 19])
+def test_composed_one_qubit_runs_match_oracle(mode, n):
+    """Runs of one-qubit gates on one qubit are composed into one matrix (FP64, host) before planning; the
+    oracle applies them one by one.  Identity products (X X, S S^dagger) are dropped."""
+    _, dtype, arith = mode
+    rng = np.random.default_rng(90 + n)
+    gates = []
+    for layer in range(4):
+        for q in range(n):
+            gates += [C.gate_u(C.rz(rng.uniform(0, 6.3)), q), C.gate_u(C.ry(rng.uniform(0, 6.3)), q),
+                      C.gate_u(C.haar_u2(rng), q)]
+        for q in range(0, n - 1, 2):
+            gates.append(C.cnot(q, q + 1) if layer % 2 == 0 else C.cnot(q + 1, (q + 2) % n))
+    gates += [C.gate_u(C.X, 0), C.gate_u(C.X, 0), C.gate_u(C.S, n - 1), C.gate_u(C.S.conj().T, n - 1)]
+    w = C.pack(gates)
+    psi0 = C.random_state(n, seed=n)
+    if dtype == B.SV_C64:
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    want = run_oracle(n, w, psi0)
+    assert_close(run_gpu(n, w, dtype, arith, psi0=psi0), want, dtype, "composed runs")
+    assert_close(run_gpu(n, w, dtype, arith, psi0=psi0, fusion=0), want, dtype, "composed runs, sweeps")
+
+
 @pytest.mark.parametrize("n,chunk_k", [(8, 8), (13, 0), (17, 0), (17, 9), (20, 12)])
 def test_c64_register_cubes_identical_to_per_gate_passes(n, chunk_k):
     """Complex64 passes apply runs of gates on at most four chunk bits from registers (SV_OPT_CUBES).  The
