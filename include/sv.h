@@ -171,8 +171,8 @@ sv_status sv_apply_gate(sv_state *s, const double *U, int target, const int *con
  *         SV_ERR_CUDA. */
 sv_status sv_apply_gate2q(sv_state *s, const double *V, int q0, int q1, const int *controls, int ncontrols);
 
-/* SWAP of qubits a and b.  Done as a relabelling of the layout map (no data movement) unless the state is
- * canonical-only (buffer states), where an in-place bit-swap pass runs. */
+/* SWAP of qubits a and b.  Done as a relabelling of the layout map (no data movement); a canonical-only
+ * (buffer) state is then put back in logical order by a bit-permutation pass at the end of the call. */
 sv_status sv_apply_swap(sv_state *s, int a, int b);
 
 /* Apply `ngates` gate records (host memory) in order.  All records are validated before any work; the
@@ -250,15 +250,15 @@ sv_status sv_renormalize(sv_state *s);
 sv_status sv_sync(sv_state *s);
 
 /* Planner statistics of the last apply call: passes launched, gates applied inside fused passes, gates
- * applied by single-gate sweeps, SWAPs folded into the layout, bit-swap passes of the apply call (buffer
- * states) plus the bit-permutation passes of canonicalisations since the state was created, and gates
- * folded into the factors of a product state (sv_init_product).  Any pointer may be NULL. */
+ * applied by single-gate sweeps, SWAPs folded into the layout, bit-permutation passes run since the call
+ * began (the canonicalisation that ends a call on a buffer state, and sv_canonicalize calls after it), and
+ * gates folded into the factors of a product state (sv_init_product).  Any pointer may be NULL. */
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
                              int *remaps, int *absorbed);
 
 /* With SV_OPT_PROFILE on: device time of the launches of the most recent apply call (or graph replay) of one
- * kind (0 = fused chunk pass, 1 = single-gate sweep, 2 = bit-swap pass), summed over its launches.  Waits for
- * those launches.  *launches = 0 when profiling is off or nothing of that kind ran. */
+ * kind (0 = fused chunk pass, 1 = single-gate sweep), summed over its launches.  Waits for those launches.
+ * *launches = 0 when profiling is off or nothing of that kind ran. */
 sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms);
 
 /* ---------------------------------------------------------------------------------------------------------

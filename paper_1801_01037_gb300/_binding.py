@@ -300,7 +300,7 @@ def sv_last_plan_stats(h: int) -> dict:
 
 
 def sv_profile_last(h: int, kind: int = 0):
-    """(launches, summed device ms) of the last apply call's launches of one kind (0 fused, 1 sweep, 2 bit swap)."""
+    """(launches, summed device ms) of the last apply call's launches of one kind (0 fused pass, 1 single-gate sweep)."""
     n, ms = ctypes.c_int(), ctypes.c_double()
     _check(load().sv_profile_last(h, kind, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value

@@ -171,10 +171,8 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st, co
       for (int i = 0; moves_only && i < d.ngates; ++i)
         moves_only = P.fused_gates[P.pass_gate_offset[step.index] + i].cls == GC_X;
       e = launch_fused(d, moves_only ? (int)MODE_C128_F64 : mode, st, f64_share_of(s), s->d_sched);
-    } else if (step.kind == Step::SWEEP) {
-      e = launch_sweep(s->psi, s->n, mode, P.sweep_gates[step.index], st);
     } else {
-      e = launch_remap_swap(s->psi, s->n, mode, step.a, step.b, st);
+      e = launch_sweep(s->psi, s->n, mode, P.sweep_gates[step.index], st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     if (evs && (e = cudaEventRecordWithFlags(evs[2 * si + 1], st, rec_flags)) != cudaSuccess)

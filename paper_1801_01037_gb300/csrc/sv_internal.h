@@ -95,7 +95,6 @@ cudaError_t launch_sweep(void *psi, int n, int mode, const DevGate &g, cudaStrea
 // SM alongside the double-float CTAs (0 = all double-float); `sched` is device scratch for that split.
 cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_share = 0, FusedSched *sched = nullptr);
 int fused_smem_bytes(int mode, int k);
-cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st);
 // Logical-order gather: out[i] = psi[phys(idx_i)], idx_i = first + i (d_idx == nullptr) or d_idx[i].
 // perm[t] = physical bit of logical qubit t.
 cudaError_t launch_gather(const void *psi, int n, int mode, const int *perm, uint64_t first, uint64_t count,

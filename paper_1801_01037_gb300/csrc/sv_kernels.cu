@@ -133,19 +133,6 @@ __global__ void k_set_one(G *psi, uint64_t x) {
   psi[x] = v;
 }
 
-// In-place exchange of index bits a and b (a < b here): psi[..1_b..0_a..] <-> psi[..0_b..1_a..].  Pure moves.
-template <typename G>
-__global__ void __launch_bounds__(256) k_remap(G *__restrict__ psi, uint64_t nitems, int lo, int hi) {
-  const uint64_t ml = 1ull << lo, mh = 1ull << hi;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t k = ((i >> lo) << (lo + 1)) | (i & (ml - 1));
-    k = ((k >> hi) << (hi + 1)) | (k & (mh - 1));
-    const G u = psi[k | ml], v = psi[k | mh];
-    psi[k | ml] = v;
-    psi[k | mh] = u;
-  }
-}
-
 struct Perm { int8_t p[kMaxQubits]; };
 
 __device__ __forceinline__ uint64_t logical_to_physical(uint64_t L, int n, const Perm &pm) {
@@ -395,15 +382,6 @@ cudaError_t launch_init_product(void *psi, int n, int mode, const double *d_fm, 
     k_product_tables<double2><<<tgrid, 256, 0, st>>>(d_fm, n, h, (double2 *)d_tab);
     k_init_product<double2><<<grid, 256, 0, st>>>((double2 *)psi, n, h, (const double2 *)d_tab);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_remap_swap(void *psi, int n, int mode, int a, int b, cudaStream_t st) {
-  const int lo = a < b ? a : b, hi = a < b ? b : a;
-  const uint64_t items = 1ull << (n - 2);
-  const unsigned grid = grid_for(items, 256);
-  if (mode == MODE_C64_F32) k_remap<float2><<<grid, 256, 0, st>>>((float2 *)psi, items, lo, hi);
-  else k_remap<double2><<<grid, 256, 0, st>>>((double2 *)psi, items, lo, hi);
   return cudaGetLastError();
 }
 

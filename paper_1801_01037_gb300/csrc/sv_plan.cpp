@@ -569,7 +569,7 @@ static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &pe
     d.ngates = (int)(P.fused_gates.size() - P.pass_gate_offset.back());
     P.step_qmask.push_back(d.qmask);
     P.passes.push_back(d);
-    P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, 0, 0, ng});
+    P.steps.push_back({Step::FUSED, (int)P.passes.size() - 1, ng});
     P.n_fused_gates += ng;
   };
   auto low_bits = [&](bool *inQ) {
@@ -604,7 +604,7 @@ static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &pe
       P.sweep_gates.push_back(to_sweep_gate(g, s));
       record_step((int)i, (int)P.steps.size());
       P.step_qmask.push_back(1ull << s.pt);
-      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+      P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 1});
       ++P.n_sweep_gates;
     }
     return;
@@ -764,7 +764,7 @@ static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &pe
         record_step(e.idx, (int)P.steps.size());
         P.step_qmask.push_back(1ull << e.pt);
         P.sweep_gates.push_back(to_sweep_gate(gates[e.idx], e));
-        P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 0, 0, 1});
+        P.steps.push_back({Step::SWEEP, (int)P.sweep_gates.size() - 1, 1});
         ++P.n_sweep_gates;
       }
       continue;

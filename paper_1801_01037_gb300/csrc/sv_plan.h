@@ -22,9 +22,8 @@ struct PlanConfig {
 };
 
 struct Step {
-  enum Kind { FUSED = 0, SWEEP = 1, REMAP = 2 } kind;
+  enum Kind { FUSED = 0, SWEEP = 1 } kind;
   int index;   // FUSED: pass index; SWEEP: sweep gate index
-  int a, b;    // REMAP: physical bits to exchange
   int ngates;  // source gates this step applies
 };
 
@@ -34,7 +33,7 @@ struct Plan {
   std::vector<int> pass_gate_offset; // first DevGate of each pass in fused_gates
   std::vector<DevGate> fused_gates;
   std::vector<DevGate> sweep_gates;
-  int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_remaps = 0, n_skipped = 0, n_merged = 0;
+  int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_skipped = 0, n_merged = 0;
   // Schedule record per source gate: the step that applies it (-1: folded into the layout or skipped) and
   // its position in execution order; per step the physical bits its chunks span (a sweep: its target bit).
   std::vector<int> gate_step, gate_order;
