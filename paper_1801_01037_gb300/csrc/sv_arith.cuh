@@ -247,6 +247,23 @@ template <> struct Arith<MODE_C128_DF32> {
       c.l[4 * i] = d.x; c.l[4 * i + 1] = d.y; c.l[4 * i + 2] = d.z; c.l[4 * i + 3] = d.w;
     }
   }
+  // Two-qubit rows read their 24 coefficient floats from the record as they are used (L1 hits), which keeps
+  // the quadruple update within the register budget.
+  static __device__ __forceinline__ S row4g(const DevGate &g, S x0, S x1, S x2, S x3) {
+    const dfv xr[4] = {{x0.x, x0.y}, {x1.x, x1.y}, {x2.x, x2.y}, {x3.x, x3.y}};
+    const dfv xi[4] = {{x0.z, x0.w}, {x1.z, x1.w}, {x2.z, x2.w}, {x3.z, x3.w}};
+    auto q = [&](int i, bool neg) {
+      const float h = g.qh[i], m = g.qm[i], l = g.ql[i];
+      return neg ? q3{-h, -m, -l} : q3{h, m, l};
+    };
+    const q3 qre[8] = {q(0, false), q(1, true), q(2, false), q(3, true), q(4, false), q(5, true), q(6, false), q(7, true)};
+    const dfv are[8] = {xr[0], xi[0], xr[1], xi[1], xr[2], xi[2], xr[3], xi[3]};
+    const dfv re = df_dot8(qre, are);
+    const q3 qim[8] = {q(0, false), q(1, false), q(2, false), q(3, false), q(4, false), q(5, false), q(6, false), q(7, false)};
+    const dfv aim[8] = {xi[0], xr[0], xi[1], xr[1], xi[2], xr[2], xi[3], xr[3]};
+    const dfv im = df_dot8(qim, aim);
+    return make_float4(re.h, re.l, im.h, im.l);
+  }
   static __device__ __forceinline__ S row4(const Coef &c, S x0, S x1, S x2, S x3) {
     const dfv xr[4] = {{x0.x, x0.y}, {x1.x, x1.y}, {x2.x, x2.y}, {x3.x, x3.y}};
     const dfv xi[4] = {{x0.z, x0.w}, {x1.z, x1.w}, {x2.z, x2.w}, {x3.z, x3.w}};

@@ -84,15 +84,23 @@ __device__ __noinline__ void chunk_quads(typename Arith<MODE>::S *sm, const DevG
     if ((j & cm) != cm) continue;
     const uint32_t s0 = slot<MODE>(j), s1 = slot<MODE>(j | b0), s2 = slot<MODE>(j | b1), s3 = slot<MODE>(j | b0 | b1);
     const S x0 = sm[s0], x1 = sm[s1], x2 = sm[s2], x3 = sm[s3];
-    typename M::Coef cf;
-    M::coef(cf, rows[0]);
-    const S r0 = M::row4(cf, x0, x1, x2, x3);
-    M::coef(cf, rows[1]);
-    const S r1 = M::row4(cf, x0, x1, x2, x3);
-    M::coef(cf, rows[2]);
-    const S r2 = M::row4(cf, x0, x1, x2, x3);
-    M::coef(cf, rows[3]);
-    const S r3 = M::row4(cf, x0, x1, x2, x3);
+    S r0, r1, r2, r3;
+    if constexpr (MODE == MODE_C128_DF32) {
+      r0 = M::row4g(rows[0], x0, x1, x2, x3);
+      r1 = M::row4g(rows[1], x0, x1, x2, x3);
+      r2 = M::row4g(rows[2], x0, x1, x2, x3);
+      r3 = M::row4g(rows[3], x0, x1, x2, x3);
+    } else {
+      typename M::Coef cf;
+      M::coef(cf, rows[0]);
+      r0 = M::row4(cf, x0, x1, x2, x3);
+      M::coef(cf, rows[1]);
+      r1 = M::row4(cf, x0, x1, x2, x3);
+      M::coef(cf, rows[2]);
+      r2 = M::row4(cf, x0, x1, x2, x3);
+      M::coef(cf, rows[3]);
+      r3 = M::row4(cf, x0, x1, x2, x3);
+    }
     sm[s0] = r0;
     sm[s1] = r1;
     sm[s2] = r2;
