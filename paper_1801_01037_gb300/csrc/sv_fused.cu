@@ -8,6 +8,7 @@
 // 256-byte rows); its other k - c bits can be any higher bits.  Every gate whose target lies in Q (and every
 // diagonal gate, wherever its target) is applied to the chunk in shared memory with the pair update of
 // Sec. V.A; control bits inside Q are tested per amplitude, control bits outside Q once per chunk.
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "sv_internal.h"
@@ -460,26 +461,31 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
 }
 
 // Largest dynamic shared-memory size already granted to kernel `fn` on the current device; raises it if
-// `bytes` is larger.  One slot per (kernel, device).
-cudaError_t ensure_smem(const void *fn, int bytes, int *granted_per_device) {
+// `bytes` is larger.  One slot per (kernel, device); several host threads may call it (the serving thread and
+// callers), so the slots are atomics and a raise keeps the larger value.
+cudaError_t ensure_smem(const void *fn, int bytes, std::atomic<int> *granted_per_device) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (bytes <= granted_per_device[dev]) return cudaSuccess;
+  if (bytes <= granted_per_device[dev].load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) granted_per_device[dev] = bytes;
+  if (e == cudaSuccess) {
+    int cur = granted_per_device[dev].load(std::memory_order_relaxed);
+    while (cur < bytes && !granted_per_device[dev].compare_exchange_weak(cur, bytes, std::memory_order_release)) {
+    }
+  }
   return e;
 }
 
-int g_sms = 0;
+// SM count of the device (one GPU per process), read once.
 int sms() {
-  if (!g_sms) {
-    int dev = 0;
+  static const int v = [] {
+    int dev = 0, count = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms < 1) g_sms = 1;
-  }
-  return g_sms;
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    return count > 0 ? count : 1;
+  }();
+  return v;
 }
 
 // The planner keeps c >= min(3, k), so the row table never has more than max(1, 2^(k-3)) entries; 128 bytes
@@ -492,7 +498,7 @@ int smem_bytes(int k) {
 template <int MODE>
 cudaError_t fused_launch(const PassDesc &p, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(p.k);
-  static int granted[64] = {0};
+  static std::atomic<int> granted[64] = {};
   cudaError_t e = ensure_smem((const void *)k_fused<MODE>, smem, granted);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -509,7 +515,7 @@ template <int MODE>
 cudaError_t fused_batch_launch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
                                int kmax, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(kmax);
-  static int granted[64] = {0};
+  static std::atomic<int> granted[64] = {};
   cudaError_t e = ensure_smem((const void *)k_fused_batch<MODE>, smem, granted);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -531,7 +537,7 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
   const uint64_t nchunks = 1ull << (p.n - p.k);
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
     const int smem = smem_bytes<MODE_C128_DF32>(p.k);
-    static int granted[64] = {0};
+    static std::atomic<int> granted[64] = {};
     cudaError_t e = ensure_smem((const void *)k_fused_mixed, smem, granted);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -558,7 +564,7 @@ cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk
   if (total == 0 || npass == 0) return cudaSuccess;
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
     const int smem = smem_bytes<MODE_C128_DF32>(kmax);
-    static int granted[64] = {0};
+    static std::atomic<int> granted[64] = {};
     cudaError_t e = ensure_smem((const void *)k_fused_batch_mixed, smem, granted);
     if (e != cudaSuccess) return e;
     int occ = 0;

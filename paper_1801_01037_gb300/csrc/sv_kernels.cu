@@ -9,16 +9,15 @@ namespace svi {
 
 namespace {
 
-int g_num_sms = 0;
-
+// SM count of the device (one GPU per process), read once; safe to call from several host threads.
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0, v = 0;
+  static const int v = [] {
+    int dev = 0, count = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    g_num_sms = v > 0 ? v : 1;
-  }
-  return g_num_sms;
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    return count > 0 ? count : 1;
+  }();
+  return v;
 }
 
 // Insert a zero bit at each of the `np` ascending positions pos[0..np).
@@ -101,11 +100,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(typename Arith<MODE>::G
 
 template <int MODE, int CLS>
 cudaError_t sweep_launch(void *psi, const SweepArgs &a, cudaStream_t st) {
-  static int occ = 0;
-  if (occ == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep<MODE, CLS>, kSweepThreads, 0);
-    if (occ < 1) occ = 1;
-  }
+  static const int occ = [] {
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sweep<MODE, CLS>, kSweepThreads, 0);
+    return o > 0 ? o : 1;
+  }();
   const uint64_t tile = (uint64_t)kSweepThreads * kSweepUnroll;
   const uint64_t need = (a.nitems + tile - 1) / tile;
   const uint64_t cap = (uint64_t)num_sms() * occ;
