@@ -144,3 +144,44 @@ def test_two_qubit_gate_is_never_folded_into_a_product_state():
         assert_close(B.sv_read_amplitudes(h), run_oracle(n, w), B.SV_C128, "product start + two-qubit gate")
     finally:
         B.sv_destroy(h)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n,chunk_k", [(6, 0), (7, 6), (9, 6), (15, 7)])
+def test_two_qubit_gates_at_small_chunks_and_four_controls(mode, n, chunk_k):
+    """Smallest chunks (k = 6, so the contiguous rows shrink to leave room for both bits), states no larger
+    than a chunk, and the maximum of four controls next to the two targets."""
+    _, dtype, arith = mode
+    rng = np.random.default_rng(40 + n + chunk_k)
+    gates = []
+    for _ in range(6):
+        q = rng.choice(n, 6, replace=False)
+        gates.append(C.gate_u4(C.haar_u4(rng), int(q[0]), int(q[1]), tuple(int(c) for c in q[2:6])))
+        gates.append(C.gate_u4(C.haar_u4(rng), int(q[1]), int(q[0])))
+        gates.append(C.gate_u(C.haar_u2(rng), int(q[2]), (int(q[3]),)))
+        gates.append(C.gate_swap(int(q[4]), int(q[5])))
+    w = C.pack(gates)
+    psi0 = C.random_state(n, seed=3 * n)
+    if dtype == B.SV_C64:
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    want = run_oracle(n, w, psi0)
+    assert_close(run_gpu(n, w, dtype, arith, psi0=psi0, chunk_k=chunk_k), want, dtype, f"n={n} k={chunk_k}")
+
+
+def test_two_qubit_gates_on_a_buffer_state_end_in_logical_order():
+    """A caller-owned buffer (always in logical order) after two-qubit gates and SWAP relabels."""
+    torch = pytest.importorskip("torch")
+    n = 16
+    rng = np.random.default_rng(61)
+    w = two_qubit_circuit(n, rng)
+    psi0 = C.random_state(n, seed=8)
+    t = torch.from_numpy(psi0).to("cuda")
+    torch.cuda.synchronize()
+    h = B.sv_create_from_buffer(n, B.SV_C128, t.data_ptr())
+    try:
+        B.sv_apply_circuit(h, w)
+        B.sv_sync(h)
+        assert list(B.sv_get_layout(h)) == list(range(n))
+        assert_close(t.cpu().numpy(), run_oracle(n, w, psi0), B.SV_C128, "buffer state")
+    finally:
+        B.sv_destroy(h)
