@@ -74,6 +74,9 @@ def test_server_results_match_oracle_under_continuous_admission():
             dt = B.SV_C64 if i % 2 else B.SV_C128
             got = B.sv_read_amplitudes(res[t]).astype(np.complex128)
             assert_close(got, run_oracle(w.n, w.gates), dt, w.name)
+            # the same circuit alone (its own state, no other request on the GPU) gives the same result
+            alone = run_gpu(w.n, w.gates, dt, B.SV_ARITH_AUTO)
+            assert_close(got, alone, dt, w.name + " in the mix vs alone")
             B.sv_destroy(res[t])
         with pytest.raises(B.SvError) as e:
             B.sv_submit(srv, 30, B.SV_C128, C.pack([]))
