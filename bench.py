@@ -592,11 +592,19 @@ def run_batched(args):
     amps_total = sum(2 ** n for n in ns)
     res = {}
     for dt, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
-        for h in B.sv_run_batch(ns[:64], dt, gl[:64]):  # warm-up: kernels, allocator
+        # chunk size from the autotuner, timed (untimed here) on a circuit of the batch's largest size
+        k = 0
+        if not args.no_autotune:
+            from paper_1801_01037_gb300 import autotune
+            probe = C.random_workload(max(ns), 6, seed=1004 + 7).gates
+            arith = B.SV_ARITH_DF32 if dt == B.SV_C128 else B.SV_ARITH_AUTO
+            k = int(autotune.tune(max(ns), dt, probe, arith, save=False)["best"])
+        ks = [k] * len(ns)
+        for h in B.sv_run_batch(ns[:64], dt, gl[:64], chunk_k=ks[:64]):  # warm-up: kernels, allocator
             B.sv_destroy(h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        hs = B.sv_run_batch(ns, dt, gl)
+        hs = B.sv_run_batch(ns, dt, gl, chunk_k=ks)
         dt_s = time.perf_counter() - t0
         # check a sample of the small circuits against the oracle
         err = 0.0
@@ -607,7 +615,7 @@ def run_batched(args):
         for h in hs:
             B.sv_destroy(h)
         res[name] = {"seconds": dt_s, "circuits_per_s": len(ws) / dt_s, "gates_per_s": gates_total / dt_s,
-                     "max_abs_err_sampled_vs_oracle": err}
+                     "chunk_qubits": k or "default", "max_abs_err_sampled_vs_oracle": err}
     print(json.dumps({"metric": "batched random circuits: circuits/s (one sv_run_batch call, end to end)",
                       "workload": f"{len(ws)} circuits, n log-uniform in [10, 22], depth 10-40 layers, seed 1004",
                       "gates": gates_total, "amplitudes": amps_total, **res}), flush=True)

@@ -271,6 +271,12 @@ sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms);
 sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
                        const size_t *ngates, void *stream, sv_state **out);
 
+/* sv_run_batch with chunk sizes: chunk_k[i] (2^k amplitudes per fused chunk, 0 = the default, else 6..13)
+ * for circuit i, e.g. from an autotuner; chunk_k may be NULL (all defaults).  Results do not depend on k
+ * beyond rounding. */
+sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
+                         const size_t *ngates, const int *chunk_k, void *stream, sv_state **out);
+
 /* A serving loop on its own host thread and stream: admits requests while their states fit in
  * hbm_budget_bytes and fewer than max_active run, and advances every admitted request by one pass per
  * iteration (continuous batching: requests join and leave between iterations). */

@@ -51,7 +51,7 @@ EXPORTED = [
     "sv_create", "sv_create_from_buffer", "sv_destroy", "sv_init_basis", "sv_init_product", "sv_write_amplitudes", "sv_set_option",
     "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_gate2q", "sv_apply_swap", "sv_apply_circuit",
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
-    "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_server_create", "sv_server_destroy",
+    "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_run_batch_k", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version",
 ]
 
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "sv_plan_dry_run": [i, i, i, P, sz, P, P, P, P, i, P],
         "sv_profile_last": [P, i, ctypes.POINTER(i), ctypes.POINTER(d)],
         "sv_run_batch": [i, P, i, P, P, P, P],
+        "sv_run_batch_k": [i, P, i, P, P, P, P, P],
         "sv_server_create": [sz, i, PP],
         "sv_server_destroy": [P],
         "sv_submit": [P, i, i, P, sz, ctypes.POINTER(u64)],
@@ -321,14 +322,20 @@ def sv_plan_dry_run(n: int, dtype: int, gates: np.ndarray, chunk_k: int = 0) -> 
             "final_perm": perm}
 
 
-def sv_run_batch(ns, dtype: int, gate_lists, stream=None) -> list:
+def sv_run_batch(ns, dtype: int, gate_lists, stream=None, chunk_k=None) -> list:
+    """Run circuits as one batch; chunk_k: optional per-circuit chunk sizes (0 = default)."""
     count = len(ns)
     arrs = [_gate_array(g) for g in gate_lists]
     n_arr = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
     ptrs = (ctypes.c_void_p * count)(*[a.ctypes.data if a.size else None for a in arrs])
     ngs = (ctypes.c_size_t * count)(*[a.size for a in arrs])
     out = (ctypes.c_void_p * count)()
-    _check(load().sv_run_batch(count, n_arr.ctypes.data, dtype, ptrs, ngs, _stream_ptr(stream), out))
+    if chunk_k is None:
+        _check(load().sv_run_batch(count, n_arr.ctypes.data, dtype, ptrs, ngs, _stream_ptr(stream), out))
+    else:
+        k_arr = np.ascontiguousarray(np.asarray(chunk_k, dtype=np.int32))
+        _check(load().sv_run_batch_k(count, n_arr.ctypes.data, dtype, ptrs, ngs, k_arr.ctypes.data,
+                                     _stream_ptr(stream), out))
     return [out[i] for i in range(count)]
 
 

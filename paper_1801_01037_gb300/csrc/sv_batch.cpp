@@ -60,9 +60,18 @@ struct DevBuf {
 
 extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
                                   const size_t *ngates, void *stream, sv_state **out) {
+  return sv_run_batch_k(count, n, dtype, gates, ngates, nullptr, stream, out);
+}
+
+extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
+                                    const size_t *ngates, const int *chunk_k, void *stream, sv_state **out) {
   if (count < 0 || (count > 0 && (!n || !gates || !ngates || !out))) return set_error(SV_ERR_ARG, "NULL argument");
   if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_ERR_ARG, "bad dtype");
   if (count == 0) return SV_OK;
+  if (chunk_k)
+    for (int i = 0; i < count; ++i)
+      if (chunk_k[i] != 0 && (chunk_k[i] < 6 || chunk_k[i] > kMaxChunkQubits))
+        return set_error(SV_ERR_ARG, "circuit " + std::to_string(i) + ": chunk qubits must be 0 or 6..13");
   int rc = check_device();
   if (rc != SV_OK) return rc;
   for (int i = 0; i < count; ++i) {
@@ -107,6 +116,7 @@ extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const
     s->psi = (char *)base + off[i];
     s->owned = false;
     s->arena = arena;
+    s->chunk_k = chunk_k ? chunk_k[i] : 0;
     states[i] = s;
   }
   // Plans are independent: several host threads make them.

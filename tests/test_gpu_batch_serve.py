@@ -86,3 +86,21 @@ def test_server_results_match_oracle_under_continuous_admission():
         assert e.value.code == B.SV_ERR_NOT_FOUND
     finally:
         B.sv_server_destroy(srv)
+
+
+def test_batch_chunk_sizes_from_a_tuner():
+    """sv_run_batch_k: per-circuit chunk sizes (as an autotuner picks them) give the oracle's results; an
+    out-of-range size is refused before any work."""
+    ws = C.batched_workloads(10, n_lo=6, n_hi=16, d_lo=2, d_hi=5, seed=91)
+    ks = [0, 6, 8, 10, 12, 13, 7, 9, 11, 13]
+    for dt in (B.SV_C128, B.SV_C64):
+        hs = B.sv_run_batch([w.n for w in ws], dt, [w.gates for w in ws], chunk_k=ks)
+        try:
+            for w, h in zip(ws, hs):
+                assert_close(B.sv_read_amplitudes(h).astype(np.complex128), run_oracle(w.n, w.gates), dt, w.name)
+        finally:
+            for h in hs:
+                B.sv_destroy(h)
+    with pytest.raises(B.SvError) as e:
+        B.sv_run_batch([w.n for w in ws], B.SV_C64, [w.gates for w in ws], chunk_k=[5] * len(ws))
+    assert e.value.code == B.SV_ERR_ARG
