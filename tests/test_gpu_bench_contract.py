@@ -41,6 +41,9 @@ def test_bench_line_has_the_contract_keys():
     assert e["value"] > 0 and e["unit"] == d["unit"] and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    acc = d["accuracy"]
+    assert acc["n"] == 16 and acc["c128_df32"]["max_abs_err"] < 1e-12 and acc["c128_f64"]["max_abs_err"] < 1e-12
+    assert acc["c64"]["one_minus_fidelity"] < 1e-8
 
 
 def test_reference_arm_line():
