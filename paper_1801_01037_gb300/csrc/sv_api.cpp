@@ -59,7 +59,9 @@ int check_device() {
 
 PlanConfig plan_config(const sv_state *s) {
   PlanConfig c;
-  if (s->dtype == SV_C64) { c.k = 13; c.c = 5; }
+  // Measured defaults (20 random layers, GB300): c128 k = 12 at every n; c64 k = 13 from n = 23 on, but
+  // k = 12 below (n = 20: 0.57 vs 0.69 ms; with fewer amplitudes the smaller chunks keep more CTAs busy).
+  if (s->dtype == SV_C64) { c.k = s->n <= 22 ? 12 : 13; c.c = 5; }
   else { c.k = 12; c.c = 4; }
   if (s->chunk_k > 0) c.k = s->chunk_k;
   c.fusion = s->fusion != 0;
