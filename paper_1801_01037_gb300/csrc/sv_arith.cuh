@@ -134,6 +134,84 @@ __device__ __forceinline__ dfv df_dot2(q3 q0, dfv x0, q3 q1, dfv x1) {
 }
 
 // ------------------------------------------------------------------------------------------------------
+// Lane-packed double-float (two independent amplitudes per value, Blackwell's packed FP32x2 instructions:
+// one instruction does the same float operation for both lanes).  The arithmetic of each lane is the
+// compensated dot product above with the same error bound; subtracted products go through TwoDiff and a
+// separate correction accumulator instead of negated coefficients, so no extra negations are needed.
+// ------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  const unsigned long long ua = ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+  const unsigned long long ub = ((unsigned long long)__float_as_uint(b.y) << 32) | __float_as_uint(b.x);
+  unsigned long long ud;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+  return make_float2(__uint_as_float((unsigned)ud), __uint_as_float((unsigned)(ud >> 32)));
+}
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+
+struct dfv2 { float2 h, l; };   // lane j: h.j + l.j
+
+// A gate entry per lane in three-float form.
+struct q3p { float2 h, m, l; };
+
+// p = q.h * x.h per lane; the product's exact rounding error and the cross terms go to c.
+__device__ __forceinline__ float2 df_term2(const q3p &q, const dfv2 &x, float2 &c) {
+  const float2 p = mul2(q.h, x.h);
+  const float2 en = fma2(make_float2(-q.h.x, -q.h.y), x.h, p);  // -(q.h x.h - p), exact
+  c = sub2(c, en);
+  c = fma2(q.h, x.l, c);
+  c = fma2(q.m, x.h, c);
+  c = fma2(q.l, x.h, c);
+  return p;
+}
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = sub2(a, b);
+  const float2 bb = sub2(s, a);
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+__device__ __forceinline__ dfv2 fast_two_sum2(float2 s, float2 c) {
+  dfv2 r;
+  r.h = add2(s, c);
+  r.l = sub2(c, sub2(r.h, s));
+  return r;
+}
+// q0 x0 - q1 x1 + q2 x2 - q3 x3 (PM) or q0 x0 + q1 x1 + q2 x2 + q3 x3, per lane.
+template <bool PM>
+__device__ __forceinline__ dfv2 df_dot4_2(const q3p &q0, const dfv2 &x0, const q3p &q1, const dfv2 &x1, const q3p &q2,
+                                          const dfv2 &x2, const q3p &q3_, const dfv2 &x3) {
+  float2 c = bcast(0.f), cn = bcast(0.f), s, e;
+  const float2 p0 = df_term2(q0, x0, c);
+  const float2 p1 = df_term2(q1, x1, PM ? cn : c);
+  const float2 p2 = df_term2(q2, x2, c);
+  const float2 p3 = df_term2(q3_, x3, PM ? cn : c);
+  if (PM) two_diff2(p0, p1, s, e); else two_sum2(p0, p1, s, e);
+  c = add2(c, e);
+  two_sum2(s, p2, s, e);
+  c = add2(c, e);
+  if (PM) two_diff2(s, p3, s, e); else two_sum2(s, p3, s, e);
+  c = add2(c, e);
+  if (PM) c = sub2(c, cn);
+  return fast_two_sum2(s, c);
+}
+template <bool PM>
+__device__ __forceinline__ dfv2 df_dot2_2(const q3p &q0, const dfv2 &x0, const q3p &q1, const dfv2 &x1) {
+  float2 c = bcast(0.f), cn = bcast(0.f), s, e;
+  const float2 p0 = df_term2(q0, x0, c);
+  const float2 p1 = df_term2(q1, x1, PM ? cn : c);
+  if (PM) two_diff2(p0, p1, s, e); else two_sum2(p0, p1, s, e);
+  c = add2(c, e);
+  if (PM) c = sub2(c, cn);
+  return fast_two_sum2(s, c);
+}
+
+// ------------------------------------------------------------------------------------------------------
 // Per-mode amplitude types.  G: element in global memory.  S: working form in registers / shared memory.
 // ------------------------------------------------------------------------------------------------------
 template <int MODE> struct Arith;
@@ -283,15 +361,20 @@ template <> struct Arith<MODE_C128_DF32> {
     const dfv xi = df_dot2(e(c, 2 * j), ai, e(c, 2 * j + 1), ar);
     return make_float4(xr.h, xr.l, xi.h, xi.l);
   }
+  // The dense pair update with both outputs in the two lanes of packed FP32x2 instructions: lane 0 computes
+  // a' = q11 a + q12 b, lane 1 computes b' = q21 a + q22 b, with the same compensated dot product per lane.
   static __device__ __forceinline__ void pair(const Coef &c, S &a, S &b) {
-    const dfv ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
-    const dfv o0r = df_dot4(e(c, 0), ar, ne(c, 1), ai, e(c, 2), br, ne(c, 3), bi);
-    const dfv o0i = df_dot4(e(c, 0), ai, e(c, 1), ar, e(c, 2), bi, e(c, 3), br);
-    const dfv o1r = df_dot4(e(c, 4), ar, ne(c, 5), ai, e(c, 6), br, ne(c, 7), bi);
-    const dfv o1i = df_dot4(e(c, 4), ai, e(c, 5), ar, e(c, 6), bi, e(c, 7), br);
-    a = make_float4(o0r.h, o0r.l, o0i.h, o0i.l);
-    b = make_float4(o1r.h, o1r.l, o1i.h, o1i.l);
+    const q3p q11r = qp(c, 0, 4), q11i = qp(c, 1, 5), q12r = qp(c, 2, 6), q12i = qp(c, 3, 7);
+    const dfv2 re = df_dot4_2<true>(q11r, bx(a.x, a.y), q11i, bx(a.z, a.w), q12r, bx(b.x, b.y), q12i, bx(b.z, b.w));
+    const dfv2 im = df_dot4_2<false>(q11r, bx(a.z, a.w), q11i, bx(a.x, a.y), q12r, bx(b.z, b.w), q12i, bx(b.x, b.y));
+    a = make_float4(re.h.x, re.l.x, im.h.x, im.l.x);
+    b = make_float4(re.h.y, re.l.y, im.h.y, im.l.y);
   }
+  // Lane pair (entry i for lane 0, entry j for lane 1) of the three-float coefficients.
+  static __device__ __forceinline__ q3p qp(const Coef &c, int i, int j) {
+    return q3p{make_float2(c.h[i], c.h[j]), make_float2(c.m[i], c.m[j]), make_float2(c.l[i], c.l[j])};
+  }
+  static __device__ __forceinline__ dfv2 bx(float h, float l) { return dfv2{bcast(h), bcast(l)}; }
 };
 
 // Apply one gate class to an amplitude pair (a = target bit 0, b = target bit 1).
