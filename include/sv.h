@@ -92,7 +92,7 @@ typedef struct sv_server sv_server;
                                    (SV_F64_SHARE_DEFAULT).
                                    Which chunks use FP64 depends only on their index: results are
                                    reproducible run to run. */
-#define SV_F64_SHARE_DEFAULT 12
+#define SV_F64_SHARE_DEFAULT 16
 #define SV_OPT_PRODUCT_START 9  /* 1 = fold leading single-qubit gates into the factors while the state is a
                                    product state (sv_init_product), the default; 0 = never (every gate runs
                                    as a kernel, e.g. to time single-gate sweeps on a fresh state) */

@@ -39,7 +39,7 @@ SV_OPT_CANONICAL = 5
 SV_OPT_PROFILE = 6
 SV_OPT_F64_SHARE = 7
 SV_OPT_CUBES = 8
-SV_F64_SHARE_DEFAULT = 12
+SV_F64_SHARE_DEFAULT = 16
 SV_OPT_PRODUCT_START = 9
 
 SV_GATE_U = 0

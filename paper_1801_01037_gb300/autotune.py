@@ -45,7 +45,7 @@ def save_cache(cache: dict) -> None:
     os.replace(tmp, p)
 
 
-F64_SHARES = (0, 8, 10, 12, 14, 16)
+F64_SHARES = (0, 10, 12, 14, 16, 18, 20)
 
 
 def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1) -> float:

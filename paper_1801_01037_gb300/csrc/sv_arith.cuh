@@ -370,6 +370,18 @@ template <> struct Arith<MODE_C128_DF32> {
     a = make_float4(re.h.x, re.l.x, im.h.x, im.l.x);
     b = make_float4(re.h.y, re.l.y, im.h.y, im.l.y);
   }
+  // The same update in scalar instructions, negated entries folded into the terms (one correction
+  // accumulator per output): the rounding of the corrections differs from the packed form in the last
+  // bits of the low word, within the same error bound.
+  static __device__ __forceinline__ void pair_scalar(const Coef &c, S &a, S &b) {
+    const dfv ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+    const dfv o0r = df_dot4(e(c, 0), ar, ne(c, 1), ai, e(c, 2), br, ne(c, 3), bi);
+    const dfv o0i = df_dot4(e(c, 0), ai, e(c, 1), ar, e(c, 2), bi, e(c, 3), br);
+    const dfv o1r = df_dot4(e(c, 4), ar, ne(c, 5), ai, e(c, 6), br, ne(c, 7), bi);
+    const dfv o1i = df_dot4(e(c, 4), ai, e(c, 5), ar, e(c, 6), bi, e(c, 7), br);
+    a = make_float4(o0r.h, o0r.l, o0i.h, o0i.l);
+    b = make_float4(o1r.h, o1r.l, o1i.h, o1i.l);
+  }
   // Lane pair (entry i for lane 0, entry j for lane 1) of the three-float coefficients.
   static __device__ __forceinline__ q3p qp(const Coef &c, int i, int j) {
     return q3p{make_float2(c.h[i], c.h[j]), make_float2(c.m[i], c.m[j]), make_float2(c.l[i], c.l[j])};
@@ -378,12 +390,16 @@ template <> struct Arith<MODE_C128_DF32> {
 };
 
 // Apply one gate class to an amplitude pair (a = target bit 0, b = target bit 1).
-template <int MODE>
+// PACK = false selects the scalar double-float pair update (same results, more instructions, fewer registers).
+template <int MODE, bool PACK = true>
 __device__ __forceinline__ void apply_pair(uint32_t cls, const typename Arith<MODE>::Coef &c,
                                            typename Arith<MODE>::S &a, typename Arith<MODE>::S &b) {
   using M = Arith<MODE>;
   switch (cls) {
-    case GC_GENERAL: M::pair(c, a, b); break;
+    case GC_GENERAL:
+      if constexpr (MODE == MODE_C128_DF32 && !PACK) M::pair_scalar(c, a, b);
+      else M::pair(c, a, b);
+      break;
     case GC_DIAG: a = M::cmul(c, 0, a); b = M::cmul(c, 3, b); break;
     case GC_PHASE: b = M::cmul(c, 3, b); break;
     case GC_ANTIDIAG: { const auto t = M::cmul(c, 1, b); b = M::cmul(c, 2, a); a = t; } break;

@@ -54,17 +54,40 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // All pairs (j0, j0 | tb) of the chunk for one gate of class CLS, target bit t, local controls cm.
-template <int MODE, int CLS>
+// PACK: dense double-float pairs in packed FP32x2 instructions (Arith::pair) or in scalar ones
+// (Arith::pair_scalar, for the batched kernels, whose extra live state made the packed form spill).
+template <int MODE, int CLS, bool PACK = true>
 __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const typename Arith<MODE>::Coef &cf,
                                             uint32_t half, int t, uint32_t tb, uint32_t cm) {
   using S = typename Arith<MODE>::S;
+  if constexpr (MODE == MODE_C128_DF32 && CLS == GC_GENERAL && PACK) {
+    if (cm == 0 && (half % (2 * kFusedThreads)) == 0) {
+      // Double-float dense gates, no local control: two pairs per thread loaded before either is computed,
+      // so their dependency chains interleave (the compiler cannot move a load above the previous pair's
+      // stores to shared memory by itself).  Pairs i and i + kFusedThreads are disjoint.
+#pragma unroll 1
+      for (uint32_t i = threadIdx.x; i < half; i += 2 * kFusedThreads) {
+        const uint32_t j0 = ins0(i, t), j1 = ins0(i + kFusedThreads, t);
+        const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
+        const uint32_t s2 = slot<MODE>(j1), s3 = slot<MODE>(j1 | tb);
+        S a = sm[s0], b = sm[s1], a1 = sm[s2], b1 = sm[s3];
+        apply_pair<MODE, PACK>(CLS, cf, a, b);
+        apply_pair<MODE, PACK>(CLS, cf, a1, b1);
+        sm[s0] = a;
+        sm[s1] = b;
+        sm[s2] = a1;
+        sm[s3] = b1;
+      }
+      return;
+    }
+  }
 #pragma unroll kPairUnroll
   for (uint32_t i = threadIdx.x; i < half; i += kFusedThreads) {
     const uint32_t j0 = ins0(i, t);
     if ((j0 & cm) != cm) continue;
     const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
     S a = sm[s0], b = sm[s1];
-    apply_pair<MODE>(CLS, cf, a, b);
+    apply_pair<MODE, PACK>(CLS, cf, a, b);
     sm[s0] = a;
     sm[s1] = b;
   }
@@ -223,7 +246,7 @@ __device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint64_t po
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
 // permuted store's table.
-template <int MODE>
+template <int MODE, bool PACK = true>
 __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, typename Arith<MODE>::S *sm,
                                             uint64_t *rowoff) {
   using M = Arith<MODE>;
@@ -315,10 +338,10 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
       } else {
         // One loop per class, so the class test is not inside the pair loop.
         switch (cls) {
-          case GC_GENERAL: chunk_pairs<MODE, GC_GENERAL>(sm, cf, half, t, tb, cm); break;
-          case GC_DIAG: chunk_pairs<MODE, GC_DIAG>(sm, cf, half, t, tb, cm); break;
-          case GC_ANTIDIAG: chunk_pairs<MODE, GC_ANTIDIAG>(sm, cf, half, t, tb, cm); break;
-          default: chunk_pairs<MODE, GC_X>(sm, cf, half, t, tb, cm); break;
+          case GC_GENERAL: chunk_pairs<MODE, GC_GENERAL, PACK>(sm, cf, half, t, tb, cm); break;
+          case GC_DIAG: chunk_pairs<MODE, GC_DIAG, PACK>(sm, cf, half, t, tb, cm); break;
+          case GC_ANTIDIAG: chunk_pairs<MODE, GC_ANTIDIAG, PACK>(sm, cf, half, t, tb, cm); break;
+          default: chunk_pairs<MODE, GC_X, PACK>(sm, cf, half, t, tb, cm); break;
         }
       }
     } else {
@@ -401,11 +424,21 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
   }
 }
 
+// A batched round's pass descriptor, copied to shared memory for the chunk (a register copy of the 104-byte
+// struct spilled).  Callers reach it after a barrier that ends the previous chunk, so no thread still reads
+// the old one.
+static_assert(sizeof(PassDesc) % 8 == 0, "PassDesc is copied in 8-byte words");
+__device__ __forceinline__ void load_pass(PassDesc &dst, const PassDesc *src) {
+  if (threadIdx.x < sizeof(PassDesc) / 8) ((uint64_t *)&dst)[threadIdx.x] = ((const uint64_t *)src)[threadIdx.x];
+  __syncthreads();
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused_batch(const PassDesc *__restrict__ passes,
                                                                const uint64_t *__restrict__ chunk_start, int npass,
                                                                uint64_t total, int kmax) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ PassDesc sp;
   using S = typename Arith<MODE>::S;
   S *sm = (S *)smraw;
   uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(S) << kmax));
@@ -415,8 +448,14 @@ __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused_bat
       const int mid = (lo + hi + 1) >> 1;
       if (chunk_start[mid] <= b) lo = mid; else hi = mid - 1;
     }
-    const PassDesc p = passes[lo];
-    fused_chunk<MODE>(p, b - chunk_start[lo], sm, rowoff);
+    if constexpr (MODE == MODE_C64_F32) {
+      // The complex64 kernel has registers to spare (no spill) and runs faster with its own copy.
+      const PassDesc p = passes[lo];
+      fused_chunk<MODE, false>(p, b - chunk_start[lo], sm, rowoff);
+    } else {
+      load_pass(sp, passes + lo);
+      fused_chunk<MODE, false>(sp, b - chunk_start[lo], sm, rowoff);
+    }
   }
 }
 
@@ -437,6 +476,7 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int role;
   __shared__ unsigned long long next;
+  __shared__ PassDesc sp;
   uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)16 << kmax));
   if (threadIdx.x == 0) {
     unsigned smid;
@@ -454,9 +494,9 @@ __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
                             : (j / rest) * 100ull + (uint64_t)share + (j % rest);
     if (c >= total) break;
     const int pi = batch_pass_of(chunk_start, npass, c);
-    const PassDesc p = passes[pi];
-    if (role) fused_chunk<MODE_C128_F64>(p, c - chunk_start[pi], (double2 *)smraw, rowoff);
-    else fused_chunk<MODE_C128_DF32>(p, c - chunk_start[pi], (float4 *)smraw, rowoff);
+    load_pass(sp, passes + pi);
+    if (role) fused_chunk<MODE_C128_F64>(sp, c - chunk_start[pi], (double2 *)smraw, rowoff);
+    else fused_chunk<MODE_C128_DF32, false>(sp, c - chunk_start[pi], (float4 *)smraw, rowoff);
   }
 }
 
