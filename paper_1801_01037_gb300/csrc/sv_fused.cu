@@ -31,6 +31,17 @@ __device__ __forceinline__ uint32_t ins0(uint32_t i, int t) {
   return ((i >> t) << (t + 1)) | (i & ((1u << t) - 1u));
 }
 
+// The i-th index, in ascending order, whose bits in `fix` equal those of `val`: the bits of i with the fixed
+// bits inserted at their positions, lowest first.  Lets a controlled gate visit only the amplitudes it
+// changes instead of testing every index.
+__device__ __forceinline__ uint32_t expand_fixed(uint32_t i, uint32_t fix, uint32_t val) {
+  for (uint32_t f = fix; f != 0u; f &= f - 1u) {
+    const uint32_t b = (uint32_t)(__ffs((int)f) - 1), low = (1u << b) - 1u;
+    i = ((i & ~low) << 1) | (val & (1u << b)) | (i & low);
+  }
+  return i;
+}
+
 #ifndef SV_FUSED_PAIR_UNROLL
 #define SV_FUSED_PAIR_UNROLL 2
 #endif
@@ -80,6 +91,20 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
       }
       return;
     }
+  }
+  if (cm != 0) {
+    // Local controls: only the half >> popc(cm) pairs whose control bits are all 1, enumerated directly.
+    const uint32_t cnt = half >> __popc(cm);
+#pragma unroll kPairUnroll
+    for (uint32_t i = threadIdx.x; i < cnt; i += kFusedThreads) {
+      const uint32_t j0 = expand_fixed(i, tb | cm, cm);
+      const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
+      S a = sm[s0], b = sm[s1];
+      apply_pair<MODE, PACK>(CLS, cf, a, b);
+      sm[s0] = a;
+      sm[s1] = b;
+    }
+    return;
   }
 #pragma unroll kPairUnroll
   for (uint32_t i = threadIdx.x; i < half; i += kFusedThreads) {
@@ -331,9 +356,11 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     if (t >= 0) {
       const uint32_t tb = 1u << t;
       if (cls == GC_PHASE) {
-        for (uint32_t i = tid; i < half; i += kFusedThreads) {
-          const uint32_t j = ins0(i, t) | tb;
-          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
+        // Only the amplitudes with the target and every local control bit set.
+        const uint32_t fix = tb | cm, cnt = nloc >> __popc(fix);
+        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+          const uint32_t j = expand_fixed(i, fix, fix);
+          sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
         }
       } else {
         // One loop per class, so the class test is not inside the pair loop.
@@ -347,12 +374,19 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     } else {
       // Diagonal gate on a qubit outside the chunk: every amplitude of the chunk has the same target bit.
       const bool one = (base & g.tmask) != 0;
+      // Entry q22 (target bit 1) or q11 (0) on the amplitudes whose local control bits are all 1 (the entry
+      // index stays a constant, so the coefficients stay in registers).
+      const uint32_t cnt = nloc >> __popc(cm);
       if (one) {
-        for (uint32_t j = tid; j < nloc; j += kFusedThreads)
-          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
+        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+          const uint32_t j = expand_fixed(i, cm, cm);
+          sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
+        }
       } else if (cls != GC_PHASE) {
-        for (uint32_t j = tid; j < nloc; j += kFusedThreads)
-          if ((j & cm) == cm) sm[slot<MODE>(j)] = M::cmul(cf, 0, sm[slot<MODE>(j)]);
+        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+          const uint32_t j = expand_fixed(i, cm, cm);
+          sm[slot<MODE>(j)] = M::cmul(cf, 0, sm[slot<MODE>(j)]);
+        }
       }
     }
     __syncthreads();
