@@ -84,6 +84,35 @@ def test_fused_circuits_match_oracle(mode, n, chunk_k):
     assert_close(got, want, dtype, f"n={n} k={chunk_k}")
 
 
+def controlled_circuit(n, rng, count=60):
+    """Gates of every class with 1-4 controls on random qubits, between Haar layers (so that the fused
+    passes see controls inside and outside the chunk, and targets of diagonal gates outside it)."""
+    gates = C.random_layers(n, 1, rng)
+    for i in range(count):
+        t = int(rng.integers(n))
+        others = [q for q in range(n) if q != t]
+        ctl = tuple(int(q) for q in rng.choice(others, size=int(rng.integers(1, 5)), replace=False))
+        u = list(class_matrices(rng).values())[i % 7]
+        gates.append(C.gate_u(u, t, ctl))
+        if i % 15 == 14:
+            gates += C.random_layers(n, 1, rng)
+    return C.pack(gates)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n,chunk_k", [(9, 0), (12, 0), (14, 0), (14, 8), (16, 6)])
+def test_fused_controlled_gates_every_class_and_control_count(mode, n, chunk_k):
+    """Controlled gates visit only the amplitudes whose local control bits are 1 (the enumerated index with
+    the control and target bits inserted): every class, 1-4 controls, against the oracle."""
+    _, dtype, arith = mode
+    rng = np.random.default_rng(31 * n + chunk_k)
+    gates = controlled_circuit(n, rng)
+    psi0 = C.random_state(n, seed=77 + n)
+    want = run_oracle(n, gates, psi0)
+    got = run_gpu(n, gates, dtype, arith, psi0, chunk_k=chunk_k)
+    assert_close(got, want, dtype, f"n={n} k={chunk_k}")
+
+
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 def test_unfused_sweeps_match_oracle(mode):
     _, dtype, arith = mode
