@@ -456,7 +456,8 @@ def run_ours(args):
         "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
                  "fused_gates_per_step": c128["stats"]["fused_gates"],
                  "folded_into_product_start": c128["stats"]["absorbed"]},
-        "roofline": {"kernel": "k_fused<c128, double-float> (fused chunk pass)", "bound": "alu",
+        "roofline": {"kernel": ("k_fused_mixed (c128 fused chunk pass: double-float CTAs + one FP64 CTA per SM)"
+                                if f64_share > 0 else "k_fused<c128, double-float> (fused chunk pass)"), "bound": "alu",
                      "achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
                      "frac": (alu_achieved / alu_peak) if alu_achieved else None, "traffic": traffic,
                      "algorithmic_ops_per_launch": ops_launch, "avg_launch_ms": avg_ms,
