@@ -134,10 +134,11 @@ __device__ __forceinline__ dfv df_dot2(q3 q0, dfv x0, q3 q1, dfv x1) {
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Lane-packed double-float (two independent amplitudes per value, Blackwell's packed FP32x2 instructions:
-// one instruction does the same float operation for both lanes).  The arithmetic of each lane is the
-// compensated dot product above with the same error bound; subtracted products go through TwoDiff and a
-// separate correction accumulator instead of negated coefficients, so no extra negations are needed.
+// Lane-packed double-float: two independent double-float values per register pair (the two outputs of a pair
+// update), computed with Blackwell's packed FP32x2 instructions (one instruction does the same float
+// operation in both lanes).  Each lane's arithmetic is the compensated dot product above with the same error
+// bound; subtracted products go through TwoDiff and a separate correction accumulator instead of negated
+// coefficients, so no extra negations are needed.
 // ------------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -200,17 +201,6 @@ __device__ __forceinline__ dfv2 df_dot4_2(const q3p &q0, const dfv2 &x0, const q
   if (PM) c = sub2(c, cn);
   return fast_two_sum2(s, c);
 }
-template <bool PM>
-__device__ __forceinline__ dfv2 df_dot2_2(const q3p &q0, const dfv2 &x0, const q3p &q1, const dfv2 &x1) {
-  float2 c = bcast(0.f), cn = bcast(0.f), s, e;
-  const float2 p0 = df_term2(q0, x0, c);
-  const float2 p1 = df_term2(q1, x1, PM ? cn : c);
-  if (PM) two_diff2(p0, p1, s, e); else two_sum2(p0, p1, s, e);
-  c = add2(c, e);
-  if (PM) c = sub2(c, cn);
-  return fast_two_sum2(s, c);
-}
-
 // ------------------------------------------------------------------------------------------------------
 // Per-mode amplitude types.  G: element in global memory.  S: working form in registers / shared memory.
 // ------------------------------------------------------------------------------------------------------
