@@ -7,7 +7,8 @@
 // Q always holds the c lowest bits, so a chunk is 2^(k-c) runs of 2^c contiguous amplitudes (coalesced
 // 256-byte rows); its other k - c bits can be any higher bits.  Every gate whose target lies in Q (and every
 // diagonal gate, wherever its target) is applied to the chunk in shared memory with the pair update of
-// Sec. V.A; control bits inside Q are tested per amplitude, control bits outside Q once per chunk.
+// Sec. V.A; control bits inside Q are inserted as fixed one-bits of the enumerated index (tested per
+// amplitude inside complex64 register cubes), control bits outside Q are tested once per chunk.
 #include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
