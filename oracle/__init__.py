@@ -55,6 +55,7 @@ def _load():
             lib.oracle_apply_gate4.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
             lib.oracle_apply_swap.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
             lib.oracle_apply_circuit.argtypes = [ctypes.c_int, P, P, ctypes.c_uint64, ctypes.c_int]
+            lib.oracle_apply_circuit_collapse.argtypes = [ctypes.c_int, P, P, ctypes.c_uint64, ctypes.c_int]
             lib.oracle_norm2.argtypes = [ctypes.c_int, P]
             lib.oracle_norm2.restype = ctypes.c_double
             lib.oracle_max_threads.restype = ctypes.c_int
@@ -124,22 +125,26 @@ def apply_swap(psi: np.ndarray, a: int, b: int) -> np.ndarray:
     return psi
 
 
-def apply_circuit(psi: np.ndarray, gates: np.ndarray, threads: int = 1) -> np.ndarray:
-    """Apply packed gate records (96-byte structured array) in order, in place; returns ``psi``."""
+def apply_circuit(psi: np.ndarray, gates: np.ndarray, threads: int = 1, collapse: bool = False) -> np.ndarray:
+    """Apply packed gate records (96-byte structured array) in order, in place; returns ``psi``.
+
+    threads > 1 splits Algorithm 1's outer loop over OpenMP threads (the paper's "outer" variant), or with
+    ``collapse`` both loops (its collapse(2) variant, which keeps gates on high qubits parallel too).  Every
+    pair is independent, so the result is the same bit for bit in every case."""
     n = _nqubits(psi)
     g = np.ascontiguousarray(gates)
     if g.dtype.itemsize != GATE_RECORD_BYTES:
         raise ValueError("gate records must be 96 bytes")
-    rc = _load().oracle_apply_circuit(n, psi.ctypes.data, g.ctypes.data if g.size else None, int(g.size),
-                                      int(threads))
+    fn = _load().oracle_apply_circuit_collapse if collapse else _load().oracle_apply_circuit
+    rc = fn(n, psi.ctypes.data, g.ctypes.data if g.size else None, int(g.size), int(threads))
     if rc != 0:
         raise ValueError(f"oracle_apply_circuit: bad gate at index {-rc - 2}" if rc <= -2 else "bad argument")
     return psi
 
 
-def simulate(n: int, gates: np.ndarray, x0: int = 0, threads: int = 1) -> np.ndarray:
+def simulate(n: int, gates: np.ndarray, x0: int = 0, threads: int = 1, collapse: bool = False) -> np.ndarray:
     """|x0> followed by the circuit: the final complex128 state vector in index order."""
-    return apply_circuit(basis_state(n, x0), gates, threads)
+    return apply_circuit(basis_state(n, x0), gates, threads, collapse)
 
 
 def norm2(psi: np.ndarray) -> float:

@@ -64,8 +64,25 @@ int oracle_init_basis(int n, double *psi, uint64_t x)
     return ORACLE_OK;
 }
 
+/* The pair update of Sec. V.A on a = alpha_k and b = alpha_{k+2^t}, both outputs from the old values:
+ * alpha_k <- q11 a + q12 b ; alpha_{k+2^t} <- q21 a + q22 b  (complex products written out). */
+static void pair_update(double *a, double *b, const double *U)
+{
+    const double q11r = U[0], q11i = U[1], q12r = U[2], q12i = U[3];
+    const double q21r = U[4], q21i = U[5], q22r = U[6], q22i = U[7];
+    const double ar = a[0], ai = a[1], br = b[0], bi = b[1];
+    a[0] = (q11r * ar - q11i * ai) + (q12r * br - q12i * bi);
+    a[1] = (q11r * ai + q11i * ar) + (q12r * bi + q12i * br);
+    b[0] = (q21r * ar - q21i * ai) + (q22r * br - q22i * bi);
+    b[1] = (q21r * ai + q21i * ar) + (q22r * bi + q22i * br);
+}
+
+/* The controlled-gate rule of Sec. V.B: the update applies only where every control bit of k is 1. */
+static int controls_on(uint64_t k, uint64_t cmask) { return (k & cmask) == cmask; }
+
 /* One gate: Algorithm 1's double loop with the controlled-gate test on each visited index. */
-static int apply_u(int n, double *psi, const double *U, int t, const int32_t *controls, int nc, int nthreads)
+static int apply_u(int n, double *psi, const double *U, int t, const int32_t *controls, int nc, int nthreads,
+                   int collapse)
 {
     if (t < 0 || t >= n || nc < 0 || nc > 4) return ORACLE_ERR_ARG;
     uint64_t cmask = 0;
@@ -77,23 +94,28 @@ static int apply_u(int n, double *psi, const double *U, int t, const int32_t *co
     const uint64_t dim = (uint64_t)1 << n;
     const uint64_t stride = (uint64_t)1 << t;           /* 2^t: distance between the two amplitudes of a pair */
     const uint64_t nblocks = dim / (2 * stride);         /* outer loop: j = 0, 2^(t+1), 2*2^(t+1), ... */
-    const double q11r = U[0], q11i = U[1], q12r = U[2], q12i = U[3];
-    const double q21r = U[4], q21i = U[5], q22r = U[6], q22i = U[7];
     (void)nthreads;
-    int64_t jb;
+    int64_t jb, kk;
+    if (collapse && nthreads > 1) {
+        /* The paper's collapse(2) variant (Sec. V.B.2): both loops of Algorithm 1 shared by the threads, so a
+         * gate on a high qubit (few outer blocks) is split as finely as one on qubit 0.  Every pair is updated
+         * exactly as below; only the thread that does it differs. */
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads)
+        for (jb = 0; jb < (int64_t)nblocks; ++jb) {
+            for (kk = 0; kk < (int64_t)stride; ++kk) {
+                const uint64_t k = (uint64_t)jb * 2 * stride + (uint64_t)kk;
+                if (!controls_on(k, cmask)) continue;
+                pair_update(psi + 2 * k, psi + 2 * (k + stride), U);
+            }
+        }
+        return ORACLE_OK;
+    }
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
     for (jb = 0; jb < (int64_t)nblocks; ++jb) {
         const uint64_t j = (uint64_t)jb * 2 * stride;
         for (uint64_t k = j; k < j + stride; ++k) {       /* inner loop: k pairs with k + 2^t */
-            if ((k & cmask) != cmask) continue;             /* controlled gate: all control bits must be 1 */
-            double *a = psi + 2 * k;
-            double *b = psi + 2 * (k + stride);
-            const double ar = a[0], ai = a[1], br = b[0], bi = b[1];
-            /* alpha_k <- q11 a + q12 b ; alpha_{k+2^t} <- q21 a + q22 b  (complex products written out) */
-            a[0] = (q11r * ar - q11i * ai) + (q12r * br - q12i * bi);
-            a[1] = (q11r * ai + q11i * ar) + (q12r * bi + q12i * br);
-            b[0] = (q21r * ar - q21i * ai) + (q22r * br - q22i * bi);
-            b[1] = (q21r * ai + q21i * ar) + (q22r * bi + q22i * br);
+            if (!controls_on(k, cmask)) continue;           /* controlled gate: all control bits must be 1 */
+            pair_update(psi + 2 * k, psi + 2 * (k + stride), U);
         }
     }
     return ORACLE_OK;
@@ -166,7 +188,7 @@ int oracle_apply_gate(int n, double *psi, const double *U, int target, const int
 {
     if (n < 1 || n > 40 || psi == NULL || U == NULL) return ORACLE_ERR_ARG;
     if (ncontrols > 0 && controls == NULL) return ORACLE_ERR_ARG;
-    return apply_u(n, psi, U, target, controls, ncontrols, 1);
+    return apply_u(n, psi, U, target, controls, ncontrols, 1, 0);
 }
 
 int oracle_apply_swap(int n, double *psi, int a, int b)
@@ -177,13 +199,14 @@ int oracle_apply_swap(int n, double *psi, int a, int b)
 
 /* A circuit is its gates applied one after another (Sec. II.B).  Returns the index of the first bad gate
  * as -(index + 2) on error, ORACLE_OK otherwise. */
-int oracle_apply_circuit(int n, double *psi, const oracle_gate *g, uint64_t ngates, int nthreads)
+static int apply_circuit(int n, double *psi, const oracle_gate *g, uint64_t ngates, int nthreads, int collapse)
 {
     if (n < 1 || n > 40 || psi == NULL || (ngates > 0 && g == NULL)) return ORACLE_ERR_ARG;
     for (uint64_t i = 0; i < ngates; ++i) {
         int rc;
         if (g[i].kind == KIND_SWAP) rc = apply_swap(n, psi, g[i].target, g[i].target2);
-        else if (g[i].kind == KIND_U) rc = apply_u(n, psi, g[i].U, g[i].target, g[i].controls, g[i].ncontrols, nthreads);
+        else if (g[i].kind == KIND_U)
+            rc = apply_u(n, psi, g[i].U, g[i].target, g[i].controls, g[i].ncontrols, nthreads, collapse);
         else if (g[i].kind == KIND_U4 && i + 3 < ngates) {
             /* the matrix's four rows come from this record and the next three */
             double V[32];
@@ -199,6 +222,18 @@ int oracle_apply_circuit(int n, double *psi, const oracle_gate *g, uint64_t ngat
         if (rc != ORACLE_OK) return -(int)(i + 2);
     }
     return ORACLE_OK;
+}
+
+int oracle_apply_circuit(int n, double *psi, const oracle_gate *g, uint64_t ngates, int nthreads)
+{
+    return apply_circuit(n, psi, g, ngates, nthreads, 0);
+}
+
+/* The same with the one-qubit gates' two loops collapsed over the threads (Sec. V.B.2's collapse variant);
+ * the result is bit-identical to the sequential one. */
+int oracle_apply_circuit_collapse(int n, double *psi, const oracle_gate *g, uint64_t ngates, int nthreads)
+{
+    return apply_circuit(n, psi, g, ngates, nthreads, 1);
 }
 
 /* Sum of |alpha_k|^2 (the normalisation condition of Sec. II.A), accumulated in index order. */

@@ -20,7 +20,7 @@ MUTANTS = {
     "sign_flip": ("(q11r * ar - q11i * ai)", "(q11r * ar + q11i * ai)"),
     "dropped_term": ("+ (q12r * bi + q12i * br);", "+ (q12r * bi);"),
     "wrong_stride": ("const uint64_t stride = (uint64_t)1 << t;", "const uint64_t stride = (uint64_t)1 << (t + 1);"),
-    "any_control_instead_of_all": ("if ((k & cmask) != cmask) continue;", "if (cmask && (k & cmask) == 0) continue;"),
+    "any_control_instead_of_all": ("return (k & cmask) == cmask;", "return cmask == 0 || (k & cmask) != 0;"),
     "reads_updated_value": ("b[0] = (q21r * ar - q21i * ai)", "b[0] = (q21r * a[0] - q21i * ai)"),
     "swap_condition": ("if ((k & ma) && !(k & mb)) {", "if (k & ma) {"),
     "u4_qubit_roles": ("idx[j] = k | ((j & 1) ? m0 : 0) | ((j & 2) ? m1 : 0);",

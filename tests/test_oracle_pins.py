@@ -315,6 +315,10 @@ def test_thread_count_does_not_change_result():
     a = oracle.simulate(n, w.gates, threads=1)
     b = oracle.simulate(n, w.gates, threads=4)
     assert np.array_equal(a, b)
+    # the collapse(2) split of both loops (used for the large parity comparisons) changes only which thread
+    # updates a pair, so it too is bit-identical, for gates on every qubit including the highest
+    c = oracle.simulate(n, w.gates, threads=4, collapse=True)
+    assert np.array_equal(a, c)
 
 
 def test_rejects_malformed_gates():
