@@ -139,7 +139,9 @@ sv_status sv_init_basis(sv_state *s, uint64_t x);
 sv_status sv_init_product(sv_state *s, const double *factors);
 
 /* Copy `count` amplitudes from host memory (state's dtype, logical order) into indices first..first+count-1
- * (checkpoint restore). */
+ * (checkpoint restore).  Errors: SV_ERR_ARG (NULL, range beyond 2^n, a non-finite component, or for complex128 a
+ * component of magnitude >= 2^126: the double-float arithmetic holds components in float exponents), checked
+ * on the host before anything is copied. */
 sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const void *host_in);
 
 sv_status sv_set_option(sv_state *s, int option, int64_t value);
@@ -181,7 +183,9 @@ sv_status sv_apply_swap(sv_state *s, int a, int b);
 sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t ngates);
 
 /* Same as sv_apply_circuit, but the gate list is captured once into a CUDA graph keyed by its contents
- * and the graph is replayed on later calls with identical gates and layout. */
+ * and the graph is replayed on later calls with identical gates and layout.  The key is a hash of the gate
+ * records, the layout, the options and the state's address; a replay also compares all of those bytes, so a
+ * hash collision only costs a new capture.  At most 64 graphs are kept per state. */
 sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngates);
 
 /* Host-only dry run of the planner for `ngates` records on n qubits of `dtype` (chunk_k = 0: the default
@@ -235,11 +239,16 @@ sv_status sv_norm(sv_state *s, double *out);
  * The per-block partial sums go to a fixed scratch array of SV_NORM_NOALLOC_MAX_PARTIALS doubles (32 KiB)
  * compiled into the library: every GPU that loads the library keeps it until the process exits.  The first
  * call on a device does a one-time set-up (it looks up that array's device address, with the device
- * current); make that first call on each device before any stream capture.  Every call writes
+ * current); make that first call on each device before any stream capture.  With CUDA's lazy module loading
+ * that look-up can be what makes the driver load the library's kernels onto the device, and the driver then
+ * allocates their code and static data (this array included) itself: a caller that hands nearly all device
+ * memory to its own pool should make one call (or any other call of this library) before reserving it.
+ * The partial count is 4 per SM of the device current at the call.  Every call writes
  * each partial it later reads, so nothing needs clearing between calls, but all calls share the one array:
  * calls whose work overlaps on the GPU (e.g. on two streams) race and give wrong results.
  * Errors: SV_ERR_ARG (NULL or misaligned pointer, n outside [1, 36], bad dtype, or a GPU whose partial-sum
- * count exceeds SV_NORM_NOALLOC_MAX_PARTIALS), SV_ERR_NO_DEVICE, SV_ERR_CUDA.  No allocation on any path. */
+ * count exceeds SV_NORM_NOALLOC_MAX_PARTIALS), SV_ERR_NO_DEVICE, SV_ERR_CUDA.  The library itself calls no
+ * allocating routine on any path (the one-time module load above is the driver's). */
 #define SV_NORM_NOALLOC_MAX_PARTIALS 4096
 sv_status sv_norm_noalloc(const void *psi, int n, sv_dtype dtype, void *stream, double *d_out);
 
@@ -277,20 +286,52 @@ sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *c
 sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
                          const size_t *ngates, const int *chunk_k, void *stream, sv_state **out);
 
+/* Statistics of the last sv_run_batch / sv_run_batch_k call of this thread: rounds (launches of the batched
+ * pass), rounds that ran in the FP64 / double-float split kernel (complex128 rounds with enough chunks to
+ * fill the GPU several times), the largest and the total chunk count of a round. */
+typedef struct sv_batch_stats {
+    uint64_t rounds, mixed_rounds, max_round_chunks, total_chunks;
+} sv_batch_stats;
+sv_status sv_last_batch_stats(sv_batch_stats *out);
+
 /* A serving loop on its own host thread and stream: admits requests while their states fit in
  * hbm_budget_bytes and fewer than max_active run, and advances every admitted request by one pass per
- * iteration (continuous batching: requests join and leave between iterations). */
+ * round (continuous batching: requests join and leave between rounds).  Each iteration of the loop launches
+ * one round per dtype that has work (complex64 and complex128 requests advance side by side), up to four
+ * rounds are queued on the server's stream ahead of the host, and admission (state allocation, planning and
+ * the gate upload) runs outside the lock that sv_submit and sv_poll take.
+ *
+ * Budget: an admitted request's state counts against hbm_budget_bytes from admission until sv_poll hands
+ * the finished state to the caller (who then owns it and frees it with sv_destroy).  A finished result that
+ * is never polled keeps holding its share of the budget. */
 sv_status sv_server_create(size_t hbm_budget_bytes, int max_active, sv_server **out);
 sv_status sv_server_destroy(sv_server *srv);
 
 /* Queue a circuit on |0...0> of n qubits; the gates are copied.  SV_ERR_BUSY when the pending queue is
- * full, SV_ERR_OOM when the state alone exceeds the budget. */
+ * full, SV_ERR_OOM when the state alone exceeds the budget.  The records are validated again when the
+ * request is admitted; a request that fails then (or whose pass descriptors fail the host's checks before a
+ * launch) reports its error through sv_poll and leaves the other requests running. */
 sv_status sv_submit(sv_server *srv, int n, sv_dtype dtype, const sv_gate *gates, size_t ngates,
                     uint64_t *ticket);
 
 /* Non-blocking: *done = 1 and *result = the final state (caller destroys it) once the request finished;
- * *done = 0 otherwise.  A finished ticket can be polled successfully once. */
+ * *done = 0 otherwise.  A finished ticket can be polled successfully once; a failed one returns its error
+ * code once (with *done = 1, *result = NULL). */
 sv_status sv_poll(sv_server *srv, uint64_t ticket, int *done, sv_state **result);
+
+/* paused = 1: admit no new request (admitted ones keep running); 0: admit again.  Lets a caller queue a
+ * burst of requests and have them admitted together. */
+sv_status sv_server_pause(sv_server *srv, int paused);
+
+typedef struct sv_server_stats {
+    uint64_t submitted, admitted, completed, failed;
+    uint64_t rounds;            /* launches of the batched pass */
+    uint64_t mixed_rounds;      /* complex128 rounds run in the FP64 / double-float split kernel */
+    uint64_t max_round_chunks;  /* largest number of chunks in one round */
+    uint64_t active, pending;   /* requests admitted and not finished; requests waiting for admission */
+    uint64_t budget_used;       /* bytes counted against the budget (see sv_server_create) */
+} sv_server_stats;
+sv_status sv_server_get_stats(sv_server *srv, sv_server_stats *out);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char *sv_last_error(void);

@@ -118,9 +118,13 @@ int ensure_scratch(sv_state *s) {
     s->d_scalars = nullptr;
     return cuda_fail(e, "state scratch allocation");
   }
-  if (!s->d_sched && (e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess) {
-    s->d_sched = nullptr;
-    return cuda_fail(e, "state scratch allocation");
+  if (!s->d_sched) {
+    if ((e = cudaMalloc(&s->d_sched, sizeof(FusedSched))) != cudaSuccess) {
+      s->d_sched = nullptr;
+      return cuda_fail(e, "state scratch allocation");
+    }
+    if ((e = cudaMemsetAsync(s->d_sched, 0, sizeof(FusedSched), s->stream)) != cudaSuccess)
+      return cuda_fail(e, "state scratch initialisation");
   }
   if (!s->stage_ev && (e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming)) != cudaSuccess) {
     s->stage_ev = nullptr;

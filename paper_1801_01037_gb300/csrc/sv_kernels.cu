@@ -161,43 +161,52 @@ __global__ void k_probs(const G *__restrict__ psi, int n, const Perm pm, uint64_
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Norm: each thread accumulates |alpha|^2 of its amplitudes as a double-float (exact float products via
-// FMA, TwoSum accumulation), the block adds the per-thread values in FP64 in a fixed tree order, and a
-// second kernel adds the per-block partials in index order: the result does not depend on timing.
+// Norm (the normalisation condition of Sec. II.A): each thread accumulates |alpha|^2 of its amplitudes in
+// native FP64 (two fused multiply-adds per amplitude on the exact double value of each component), the block
+// adds the per-thread values in FP64 in a fixed tree order, and a second kernel adds the per-block partials in
+// index order: the result does not depend on timing.
 // ------------------------------------------------------------------------------------------------------
 constexpr int kNormThreads = 256;
 constexpr int kNormBlocksPerSm = 4;
 
-// Adds sg * (h + l)^2 to the double-float accumulator (s, c); sg = +-1 (exact sign flip).
-__device__ __forceinline__ void acc_sq(float &s, float &c, float h, float l, float sg) {
-  const float p = __fmul_rn(h, h) * sg;
-  float e = __fmaf_rn(h * sg, h, -p);
-  e = __fmaf_rn(2.0f * h * sg, l, e);
-  float s2, err;
-  two_sum(s, p, s2, err);
-  s = s2;
-  c = __fadd_rn(c, __fadd_rn(err, e));
+// The exact double value of a float, with integer operations (the float -> double conversion instruction runs
+// on GB300's slow FP64/conversion unit).  Normal floats: sign, exponent re-biased by 1023 - 127, mantissa
+// shifted into place; subnormal floats (below 2^-126), zeros, infinities and NaNs take the conversion
+// instruction (a branch that normalised states never take, apart from exact zeros).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = b & 0x7F800000u;
+  if (e == 0u || e == 0x7F800000u) return (double)f;
+  const uint32_t hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(b << 29));
 }
 
-// Stage 1 of sum_k (-1)^popcount(k & pmask) |psi_k|^2 over physical indices k (pmask = 0: the norm).
+__device__ __forceinline__ double flip_if(double x, bool neg) {
+  return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
+}
+
+// Stage 1 of sum_k (-1)^popcount(k & pmask) |psi_k|^2 over physical indices k (pmask = 0: the norm).  The sign
+// is applied by flipping one factor's sign bit (exact), so each term is one FP64 multiply-add.
 template <typename G, bool IS_DOUBLE>
 __global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ psi, uint64_t N, uint64_t pmask,
                                                         double *__restrict__ partials) {
-  float s = 0.f, c = 0.f;
+  double acc = 0.0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     const G v = psi[i];
-    const float sg = (__popcll(i & pmask) & 1) ? -1.0f : 1.0f;
-    if (IS_DOUBLE) {
-      const dfv r = df_split((double)v.x), m = df_split((double)v.y);
-      acc_sq(s, c, r.h, r.l, sg);
-      acc_sq(s, c, m.h, m.l, sg);
+    const bool neg = (__popcll(i & pmask) & 1) != 0;
+    double x, y;
+    if constexpr (IS_DOUBLE) {
+      x = (double)v.x;
+      y = (double)v.y;
     } else {
-      acc_sq(s, c, (float)v.x, 0.f, sg);
-      acc_sq(s, c, (float)v.y, 0.f, sg);
+      x = f2d_exact((float)v.x);
+      y = f2d_exact((float)v.y);
     }
+    acc = __fma_rn(flip_if(x, neg), x, acc);
+    acc = __fma_rn(flip_if(y, neg), y, acc);
   }
   __shared__ double red[kNormThreads];
-  red[threadIdx.x] = (double)s + (double)c;
+  red[threadIdx.x] = acc;
   __syncthreads();
   for (int w = kNormThreads / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -410,9 +419,15 @@ cudaError_t launch_probs(const void *psi, int n, int mode, const int *perm, uint
 
 int norm_parts() { return num_sms() * kNormBlocksPerSm; }
 
+int norm_parts_for_sms(int sms) { return (sms > 0 ? sms : 1) * kNormBlocksPerSm; }
+
 cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
                         uint64_t pmask) {
-  const int parts = norm_parts();
+  return launch_norm_parts(psi, n, mode, d_partials, d_out, st, pmask, norm_parts());
+}
+
+cudaError_t launch_norm_parts(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
+                              uint64_t pmask, int parts) {
   const uint64_t N = 1ull << n;
   if (mode == MODE_C64_F32)
     k_norm1<float2, false><<<parts, kNormThreads, 0, st>>>((const float2 *)psi, N, pmask, d_partials);

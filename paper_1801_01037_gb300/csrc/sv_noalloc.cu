@@ -52,13 +52,18 @@ extern "C" sv_status sv_norm_noalloc(const void *psi, int n, sv_dtype dtype, voi
   if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
   int rc = check_device();
   if (rc != SV_OK) return rc;
-  const int parts = norm_parts();
+  // Partial count from the SM count of the device current now (the caller may switch devices between calls).
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+  const int parts = norm_parts_for_sms(sms);
   if (parts > SV_NORM_NOALLOC_MAX_PARTIALS)
     return set_error(SV_ERR_ARG, "this GPU needs " + std::to_string(parts) + " partial sums; the fixed scratch holds " +
                                      std::to_string(SV_NORM_NOALLOC_MAX_PARTIALS));
   double *partials = nullptr;
   if ((rc = scratch_for_current_device(&partials)) != SV_OK) return rc;
   const int mode = dtype == SV_C64 ? MODE_C64_F32 : MODE_C128_DF32;
-  cudaError_t e = launch_norm(psi, n, mode, partials, d_out, (cudaStream_t)stream);
+  e = launch_norm_parts(psi, n, mode, partials, d_out, (cudaStream_t)stream, 0, parts);
   return e == cudaSuccess ? SV_OK : cuda_fail(e, "norm launch");
 }

@@ -1,5 +1,7 @@
 // C ABI: read-out in logical order, checkpoint write, norm, renormalisation and the CUDA-graph apply path.
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -130,6 +132,19 @@ sv_status sv_write_amplitudes(sv_state *s, uint64_t first, uint64_t count, const
   if (!s || (!host_in && count)) return set_error(SV_ERR_ARG, "NULL argument");
   int rc = check_range(s, first, count);
   if (rc != SV_OK) return rc;
+  // Every component must be finite; complex128 components must also lie below 2^126 in magnitude, the range
+  // in which the double-float working form (float exponents) and the sums of a pair update cannot overflow.
+  if (s->dtype == SV_C128) {
+    const double *v = (const double *)host_in;
+    for (uint64_t i = 0; i < 2 * count; ++i)
+      if (!std::isfinite(v[i]) || std::fabs(v[i]) >= 0x1p126)
+        return set_error(SV_ERR_ARG, "amplitude " + std::to_string(first + i / 2) +
+                                         " is not finite or has a component of magnitude >= 2^126");
+  } else {
+    const float *v = (const float *)host_in;
+    for (uint64_t i = 0; i < 2 * count; ++i)
+      if (!std::isfinite(v[i])) return set_error(SV_ERR_ARG, "amplitude " + std::to_string(first + i / 2) + " is not finite");
+  }
   if (!identity_layout(s) && (rc = canonicalize_now(s)) != SV_OK) return rc;
   s->product = false;
   const size_t ab = amp_bytes(s->dtype);
@@ -249,22 +264,33 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
     return SV_OK;
   }
   const PlanConfig cfg = plan_config(s);
-  uint64_t key = 1469598103934665603ull;
-  key = hash_bytes(gates, ngates * sizeof(sv_gate), key);
-  key = hash_bytes(s->perm.data(), s->perm.size() * sizeof(int), key);
+  // The key material: gate records, layout, options and the state's address, hashed (FNV-1a) to find the
+  // entry and compared byte for byte before a replay.
   const int opts[8] = {s->n, mode_of(s), cfg.k, cfg.c, (int)cfg.fusion, s->canonical, f64_share_of(s), (int)cfg.cubes};
-  key = hash_bytes(opts, sizeof opts, key);
-  key = hash_bytes(&s->psi, sizeof s->psi, key);
+  std::vector<unsigned char> kb(ngates * sizeof(sv_gate) + s->perm.size() * sizeof(int) + sizeof opts + sizeof s->psi);
+  {
+    unsigned char *q = kb.data();
+    if (ngates) std::memcpy(q, gates, ngates * sizeof(sv_gate));
+    q += ngates * sizeof(sv_gate);
+    std::memcpy(q, s->perm.data(), s->perm.size() * sizeof(int));
+    q += s->perm.size() * sizeof(int);
+    std::memcpy(q, opts, sizeof opts);
+    q += sizeof opts;
+    std::memcpy(q, &s->psi, sizeof s->psi);
+  }
+  uint64_t key = hash_bytes(kb.data(), kb.size(), 1469598103934665603ull);
+  // Test hook: with SV_TEST_GRAPH_KEY_COLLIDE set every circuit gets the same key, as a hash collision would.
+  if (std::getenv("SV_TEST_GRAPH_KEY_COLLIDE")) key = 42;
   auto it = s->graphs.find(key);
   cudaError_t e;
-  if (it != s->graphs.end() && it->second.perm_before == s->perm && (it->second.evs.empty() != (s->profile != 0))) {
+  if (it != s->graphs.end() && it->second.key_bytes == kb && (it->second.evs.empty() != (s->profile != 0))) {
     if ((e = cudaGraphLaunch(it->second.exec, s->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
     s->perm = it->second.perm_after;
     s->last_evs = it->second.evs.empty() ? nullptr : it->second.evs.data();
     s->last_kind = it->second.ev_kind;
     return SV_OK;
   }
-  if (it != s->graphs.end()) {  // same key captured with the other profiling setting: replace it
+  if (it != s->graphs.end()) {  // same key with other contents (a collision) or profiling setting: replace it
     cudaStreamSynchronize(s->stream);
     free_entry(it->second);
     s->graphs.erase(it);
@@ -276,6 +302,7 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   }
   GraphEntry ent;
   ent.perm_before = s->perm;
+  ent.key_bytes = std::move(kb);
   std::vector<int> perm = s->perm;
   Plan P;
   make_plan(s->n, cfg, perm, gates, ngates, P);

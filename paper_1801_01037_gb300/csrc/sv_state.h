@@ -17,6 +17,9 @@ struct GraphEntry {
   std::vector<int> ev_kind;
   std::vector<int> perm_before, perm_after;
   size_t nbytes = 0;
+  // Everything the key hashes (gate records, layout, options, state address), kept so that a lookup compares
+  // the bytes themselves and a hash collision can never replay another circuit's graph.
+  std::vector<unsigned char> key_bytes;
 };
 
 struct sv_state {
