@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--served-rates", default="10,30,100", help="request rates (per s) to sweep")
     ap.add_argument("--served-count", type=int, default=200, help="requests per rate")
+    ap.add_argument("--served-rate", type=float, default=30.0, help="rate of the served sample in the default line")
+    ap.add_argument("--served-requests", type=int, default=100, help="requests of the served sample in the default line")
+    ap.add_argument("--no-extra", action="store_true", help="skip the served and batched samples of the default line")
+    ap.add_argument("--no-n33", action="store_true", help="skip the n = 33 single-gate sweep")
     return ap.parse_args()
 
 
@@ -159,17 +163,24 @@ class OracleRunner:
                 f"FP64 oracle (Algorithm 1 loop, outer loop over {self.threads} OpenMP threads), from |0...0>")
 
 
+RENORM_PERIOD = 64
+
+
 def gpu_results_for_accuracy(B, n_acc, depth):
     """The GPU's final states for the bench's circuit family at a size the host oracle finishes in seconds:
-    complex128 double-float (with the FP64 share), all-FP64, and complex64.  Compared in the CPU leg."""
+    complex128 double-float (with the FP64 share), all-FP64, and complex64 without and with periodic
+    renormalisation (every RENORM_PERIOD gates, FP64 norm).  Compared in the CPU leg."""
     w = C.random_workload(n_acc, depth, seed=SEED)
     res = {}
-    for name, dt, arith in (("c128_df32", B.SV_C128, B.SV_ARITH_DF32), ("c128_f64", B.SV_C128, B.SV_ARITH_F64),
-                            ("c64", B.SV_C64, B.SV_ARITH_AUTO)):
+    for name, dt, arith, renorm in (("c128_df32", B.SV_C128, B.SV_ARITH_DF32, 0),
+                                    ("c128_f64", B.SV_C128, B.SV_ARITH_F64, 0),
+                                    ("c64", B.SV_C64, B.SV_ARITH_AUTO, 0),
+                                    ("c64_renorm", B.SV_C64, B.SV_ARITH_AUTO, RENORM_PERIOD)):
         h = B.sv_create(n_acc, dt)
         try:
             if dt == B.SV_C128:
                 B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            B.sv_set_option(h, B.SV_OPT_RENORM_PERIOD, renorm)
             B.sv_apply_circuit(h, w.gates)
             res[name] = B.sv_read_amplitudes(h).astype(np.complex128)
         finally:
@@ -186,9 +197,15 @@ def cpu_leg_accuracy(n_acc, depth, w, gpu_states):
     dt = time.perf_counter() - t0
     out = {"n": n_acc, "layers": depth, "reference": "FP64 oracle, full state",
            "oracle_seconds": dt, "oracle_gates_per_s": len(w.gates) / dt}
+    scale = float(np.max(np.abs(want)))
     for name, got in gpu_states.items():
         fid = abs(np.vdot(want, got)) ** 2 / (np.vdot(want, want).real * np.vdot(got, got).real)
-        out[name] = {"max_abs_err": float(np.max(np.abs(got - want))), "one_minus_fidelity": float(max(0.0, 1.0 - fid))}
+        err = float(np.max(np.abs(got - want)))
+        out[name] = {"max_abs_err": err, "max_abs_err_rel": err / scale,
+                     "one_minus_fidelity": float(max(0.0, 1.0 - fid)),
+                     "norm_deviation": float(abs(np.vdot(got, got).real - 1.0))}
+    out["max_abs_psi"] = scale
+    out["renorm_period_gates"] = RENORM_PERIOD
     return out
 
 
@@ -302,17 +319,19 @@ def run_ours(args):
             if dt == B.SV_C128:
                 f64_share = int(res["best_f64_share"])
 
-    def timed(dtype, arith, steps, warmup, profile=False, sampler=None):
+    def timed(dtype, arith, steps, warmup, profile=False, sampler=None, renorm=0):
         h = B.sv_create(args.n, dtype)
         try:
+            B.sv_set_option(h, B.SV_OPT_RENORM_PERIOD, renorm)
             if dtype == B.SV_C128:
                 B.sv_set_option(h, B.SV_OPT_ARITH, arith)
                 B.sv_set_option(h, B.SV_OPT_F64_SHARE, f64_share)
             if dtype in chunk_k:
                 B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k[dtype])
             B.sv_set_option(h, B.SV_OPT_PROFILE, 1 if profile else 0)
+            graph = renorm == 0  # renormalisation runs between launches, so not inside a captured graph
             for _ in range(warmup):
-                step(h)
+                step(h, graph)
             torch.cuda.synchronize()
             barrier(dist)
             torch.cuda.synchronize()
@@ -322,7 +341,7 @@ def run_ours(args):
                 sampler.start()
             e0.record()
             for _ in range(steps):
-                nrm, _ = step(h)
+                nrm, _ = step(h, graph)
                 if profile:
                     l, ms = B.sv_profile_last(h, 0)
                     fused_launches += l
@@ -338,15 +357,16 @@ def run_ours(args):
         finally:
             B.sv_destroy(h)
 
-    def sweep_roofline(dtype, arith, u, label, peak):
+    def sweep_roofline(dtype, arith, u, label, peak, n=None):
         """Single-gate sweeps (the unfused path) on targets spread over all qubits, timed per launch."""
-        h = B.sv_create(args.n, dtype)
+        n = n or args.n
+        h = B.sv_create(n, dtype)
         try:
             if dtype == B.SV_C128:
                 B.sv_set_option(h, B.SV_OPT_ARITH, arith)
             B.sv_set_option(h, B.SV_OPT_PROFILE, 1)
             B.sv_set_option(h, B.SV_OPT_PRODUCT_START, 0)  # every gate is a sweep launch, even on |0...0>
-            targets = sorted({0, 1, args.n // 4, args.n // 2, 3 * args.n // 4, args.n - 2, args.n - 1})
+            targets = sorted({0, 1, n // 4, n // 2, 3 * n // 4, n - 2, n - 1})
             for t in targets[:2]:
                 B.sv_apply_gate(h, u, t)
             ms_list = []
@@ -354,10 +374,11 @@ def run_ours(args):
                 B.sv_apply_gate(h, u, t)
                 _, ms = B.sv_profile_last(h, 1)
                 ms_list.append(ms)
-            ab = (8 if dtype == B.SV_C64 else 16) << args.n
+            ab = (8 if dtype == B.SV_C64 else 16) << n
             avg = sum(ms_list) / len(ms_list)
             ach = 2 * ab / (avg * 1e-3) / 1e9
-            return {"kernel": f"k_sweep ({label})", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            return {"kernel": f"k_sweep ({label}), n={n}", "n": n, "bound": "hbm", "achieved": ach, "peak": peak,
+                    "unit": "GB/s",
                     "frac": ach / peak, "avg_launch_ms": avg, "algorithmic_bytes_per_launch": 2 * ab,
                     "targets": targets, "per_target_ms": [round(x, 3) for x in ms_list]}
         finally:
@@ -400,6 +421,13 @@ def run_ours(args):
     sweeps = [sweep_roofline(B.SV_C128, B.SV_ARITH_DF32, u_dense, "c128 dense U(2), double-float", peak),
               sweep_roofline(B.SV_C128, B.SV_ARITH_DF32, C.X, "c128 X, moves", peak),
               sweep_roofline(B.SV_C64, B.SV_ARITH_AUTO, u_dense, "c64 dense U(2)", peak)]
+    # the same complex128 sweep on the 128 GiB state of n = 33 (spec range n = 30-33), when it fits
+    if args.n == N_QUBITS and not args.no_n33:
+        import torch
+        free_b, _ = torch.cuda.mem_get_info()
+        if free_b >= (16 << 33) + (2 << 30):
+            sweeps.append(sweep_roofline(B.SV_C128, B.SV_ARITH_DF32, u_dense, "c128 dense U(2), double-float", peak,
+                                         n=33))
     avg_ms = c128["fused_ms"] / max(1, c128["fused_launches"])
     hbm_achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9 if c128["fused_launches"] else None
     # FP32-pipe roofline of the fused pass (it is bound by instruction issue, not by HBM).  With `f64_share`
@@ -421,6 +449,19 @@ def run_ours(args):
     folded_start = c128["stats"]["absorbed"] > 0
     launches_per_step = (1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
                          + (2 if folded_start else 0))
+    # The other configurations of the metric, measured after the timed region: a bounded served stream
+    # (complex64, 150 GB budget) and a 512-circuit batch per dtype (chunk sizes per size class of n).
+    served = batched = None
+    if not args.no_extra:
+        served = served_measure(B, args.served_rate, args.served_requests)
+        ws_b = C.batched_workloads(512, seed=1004)
+        batched = {}
+        for dt_b, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
+            ks, picked = batch_chunk_sizes(B, [w.n for w in ws_b], dt_b, not args.no_autotune)
+            batched[name] = {**batched_measure(B, ws_b, dt_b, ks), "chunk_qubits": picked or "default"}
+        batched["workload"] = "512 random circuits, n log-uniform in [10, 22], 10-40 layers, seed 1004"
+    # c64 with periodic renormalisation (every RENORM_PERIOD gates), one step, for its cost beside c64 without
+    c64_renorm = timed(B.SV_C64, B.SV_ARITH_AUTO, 1, 1, renorm=RENORM_PERIOD)
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
     accuracy = None
     if RANK == 0:
@@ -430,6 +471,9 @@ def run_ours(args):
 
     if RANK != 0:
         return
+    # FP64-equivalent work of the method (16 flops per touched amplitude of a dense 2x2 gate, 6 per touched
+    # amplitude of a diagonal one, none for an exchange) per fused launch
+    flops_launch = 2.0 * f64_fmas_per_step(kernel_gates, args.n) / max(1, c128["stats"]["passes"])
     line = {
         "metric": f"gates/s, n={args.n} random circuit ({args.depth} layers), complex128",
         "value": value,
@@ -447,30 +491,44 @@ def run_ours(args):
         "config": {**workload_config(args),
                    "chunk_qubits": {"c128": chunk_k.get(B.SV_C128, "default 12"), "c64": chunk_k.get(B.SV_C64, "default 13")},
                    "autotune_ms": tuning},
-        "effective_hbm_gbs": value * 2 * state_bytes / 1e9 / WORLD,
+        "f64_native": None if f64 is None else {"value": G / (f64["ms"] / 1e3), "unit": "gates/s",
+                                                 "ms_per_step": f64["ms"],
+                                                 "note": "the same step with IEEE FP64 arithmetic throughout "
+                                                         "(SV_ARITH_F64), 1 timed step after 1 warm-up"},
         "c64": {"value": total_gates / c64_t, "unit": "gates/s",
                 "ms_per_step": c64_t * 1e3 / args.steps,
-                "effective_hbm_gbs": G * args.steps / c64_t * 2 * (8 << args.n) / 1e9},
-        "f64_native": None if f64 is None else {"value": G / (f64["ms"] / 1e3), "unit": "gates/s",
-                                                 "ms_per_step": f64["ms"], "note": "c128 with FP64 arithmetic, 1 step"},
+                "effective_hbm_gbs": G * args.steps / c64_t * 2 * (8 << args.n) / 1e9,
+                "with_renormalisation": {"period_gates": RENORM_PERIOD, "ms_per_step": c64_renorm["ms"],
+                                         "value": G / (c64_renorm["ms"] / 1e3), "unit": "gates/s",
+                                         "note": "1 step, direct launches (renormalisation between launches)"}},
+        "effective_hbm_gbs": value * 2 * state_bytes / 1e9 / WORLD,
+        "served": served,
+        "batched": batched,
         "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
                  "fused_gates_per_step": c128["stats"]["fused_gates"],
                  "folded_into_product_start": c128["stats"]["absorbed"]},
+        # The method's roofline of the dominant kernel (algorithmic bytes: one read and one write of the state
+        # per fused pass, against the measured HBM copy bandwidth).  The pass is limited by arithmetic issue, not
+        # by HBM: its FP32-pipe and FP64-pipe views follow, and its FP64-equivalent flop rate.
         "roofline": {"kernel": ("k_fused_mixed (c128 fused chunk pass: double-float CTAs + one FP64 CTA per SM)"
-                                if f64_share > 0 else "k_fused<c128, double-float> (fused chunk pass)"), "bound": "alu",
-                     "achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
-                     "frac": (alu_achieved / alu_peak) if alu_achieved else None, "traffic": traffic,
-                     "algorithmic_ops_per_launch": ops_launch, "avg_launch_ms": avg_ms,
-                     "launches_timed": c128["fused_launches"],
-                     "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
+                                if f64_share > 0 else "k_fused<c128, double-float> (fused chunk pass)"),
+                     "bound": "hbm", "achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (hbm_achieved / peak) if hbm_achieved else None, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": 2 * state_bytes, "avg_launch_ms": avg_ms,
+                     "launches_timed": c128["fused_launches"], "peak_source": f"{peak_kind} hbm_gbs",
+                     "limited_by": "FP32-pipe issue of the double-float arithmetic (see alu_view)",
+                     "fp64_equivalent": {"flops_per_launch": flops_launch,
+                                         "achieved_tflops": (flops_launch / (avg_ms * 1e-3) / 1e12) if hbm_achieved else None,
+                                         "note": "16 flops per touched amplitude of a dense gate, 6 of a diagonal one"},
+                     "alu_view": {"achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
+                                  "frac": (alu_achieved / alu_peak) if alu_achieved else None,
+                                  "algorithmic_ops_per_launch": ops_launch,
+                                  "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
+                                  "note": "operations of the double-float method itself (its chosen arithmetic)"},
                      "f64_share_percent": f64_share,
                      "fp64_pipe_view": {"achieved": f64_achieved, "peak": f64_peak, "unit": "T FP64 FMA/s",
                                         "frac": (f64_achieved / f64_peak) if f64_achieved else None,
-                                        "peak_source": "152 SMs x 1.73 FP64 FMA/clock (probe) x median SM clock"},
-                     "hbm_view": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
-                                  "frac": (hbm_achieved / peak) if hbm_achieved else None,
-                                  "algorithmic_bytes_per_launch": 2 * state_bytes,
-                                  "peak_source": f"{peak_kind} hbm_gbs"}},
+                                        "peak_source": "152 SMs x 1.73 FP64 FMA/clock (probe) x median SM clock"}},
         "sweep_roofline": sweeps,
         "cpu_baseline": cpu,
         "accuracy": accuracy,
@@ -617,77 +675,97 @@ def run_single_config(args):
           flush=True)
 
 
+SIZE_CLASSES = ((0, 13), (14, 17), (18, 99))
+
+
+def batch_chunk_sizes(B, ns, dt, tune):
+    """Chunk size per circuit: for each size class of n (up to 13, 14-17, 18 and up) the autotuner times the
+    candidate k (and, for complex128, the FP64 share) on a 6-layer random circuit at the class's largest n in
+    the batch; every circuit of the class gets that k.  tune=False: the library default (0) for all."""
+    if not tune:
+        return [0] * len(ns), {}
+    from paper_1801_01037_gb300 import autotune
+    arith = B.SV_ARITH_DF32 if dt == B.SV_C128 else B.SV_ARITH_AUTO
+    ks, picked = [0] * len(ns), {}
+    for lo, hi in SIZE_CLASSES:
+        members = [i for i, n in enumerate(ns) if lo <= n <= hi]
+        if not members:
+            continue
+        n_rep = max(ns[i] for i in members)
+        probe = C.random_workload(n_rep, 6, seed=1004 + 7).gates
+        k = int(autotune.tune(n_rep, dt, probe, arith, save=False)["best"])
+        picked[f"n{lo}-{min(hi, max(ns))}"] = {"tuned_at_n": n_rep, "k": k}
+        for i in members:
+            ks[i] = k
+    return ks, picked
+
+
+def batched_measure(B, ws, dt, ks):
+    """One sv_run_batch_k call over all circuits, end to end on the host clock (plan, allocate, upload, the
+    captured rounds, synchronise), after a warm-up call on the first 64 circuits."""
+    import torch
+    ns, gl = [w.n for w in ws], [w.gates for w in ws]
+    for h in B.sv_run_batch(ns[:64], dt, gl[:64], chunk_k=ks[:64]):  # warm-up: kernels, allocator
+        B.sv_destroy(h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = B.sv_run_batch(ns, dt, gl, chunk_k=ks)
+    dt_s = time.perf_counter() - t0
+    st = B.sv_last_batch_stats()
+    # a property of every result (unitary circuits keep the norm at 1); parity with the oracle is tested in
+    # tests/test_gpu_batch_serve.py
+    dev = max(abs(B.sv_norm(h) - 1.0) for h in hs)
+    for h in hs:
+        B.sv_destroy(h)
+    gates_total = sum(len(g) for g in gl)
+    return {"circuits": len(ws), "seconds": dt_s, "circuits_per_s": len(ws) / dt_s, "gates_per_s": gates_total / dt_s,
+            "rounds": st["rounds"], "mixed_rounds": st["mixed_rounds"], "max_round_chunks": st["max_round_chunks"],
+            "max_norm_deviation": dev}
+
+
 def run_batched(args):
     """4096 independent random circuits (n log-uniform in [10, 22], 10-40 layers, seed 1004) in one
-    sv_run_batch call per dtype; the call plans, allocates, uploads, runs and synchronises."""
-    import torch
+    sv_run_batch_k call per dtype, chunk sizes from the autotuner per size class of n."""
     from paper_1801_01037_gb300 import build as sv_build
     sv_build.build()
     from paper_1801_01037_gb300 import _binding as B
     B.load()
     ws = C.batched_workloads(args.batch_count, seed=1004)
-    ns, gl = [w.n for w in ws], [w.gates for w in ws]
-    gates_total = sum(len(g) for g in gl)
-    amps_total = sum(2 ** n for n in ns)
+    ns = [w.n for w in ws]
     res = {}
     for dt, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
-        # chunk size from the autotuner, timed (untimed here) on a circuit of the batch's largest size
-        k = 0
-        if not args.no_autotune:
-            from paper_1801_01037_gb300 import autotune
-            probe = C.random_workload(max(ns), 6, seed=1004 + 7).gates
-            arith = B.SV_ARITH_DF32 if dt == B.SV_C128 else B.SV_ARITH_AUTO
-            k = int(autotune.tune(max(ns), dt, probe, arith, save=False)["best"])
-        ks = [k] * len(ns)
-        for h in B.sv_run_batch(ns[:64], dt, gl[:64], chunk_k=ks[:64]):  # warm-up: kernels, allocator
-            B.sv_destroy(h)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hs = B.sv_run_batch(ns, dt, gl, chunk_k=ks)
-        dt_s = time.perf_counter() - t0
-        # a property of every result (unitary circuits keep the norm at 1); parity with the oracle is tested in
-        # tests/test_gpu_batch_serve.py
-        dev = max(abs(B.sv_norm(h) - 1.0) for h in hs)
-        for h in hs:
-            B.sv_destroy(h)
-        res[name] = {"seconds": dt_s, "circuits_per_s": len(ws) / dt_s, "gates_per_s": gates_total / dt_s,
-                     "chunk_qubits": k or "default", "max_norm_deviation": dev}
+        ks, picked = batch_chunk_sizes(B, ns, dt, not args.no_autotune)
+        res[name] = {**batched_measure(B, ws, dt, ks), "chunk_qubits": picked or "default"}
     print(json.dumps({"metric": "batched random circuits: circuits/s (one sv_run_batch call, end to end)",
                       "workload": f"{len(ws)} circuits, n log-uniform in [10, 22], depth 10-40 layers, seed 1004",
-                      "gates": gates_total, "amplitudes": amps_total, **res}), flush=True)
+                      "gates": sum(len(w.gates) for w in ws), "amplitudes": sum(2 ** n for n in ns), **res}),
+          flush=True)
 
 
-def run_served(args):
-    """Poisson arrivals through the serving loop (150 GB budget), complex64; per rate: circuits/s and
-    latency percentiles (completion seen by sv_poll minus scheduled arrival)."""
+def served_measure(B, rate, count, budget=150 * 10 ** 9, max_active=512):
+    """Poisson arrivals (seed 1005) through the serving loop, complex64: circuits/s over the stream and latency
+    percentiles (completion seen by sv_poll minus scheduled arrival)."""
     import threading
-    import torch
-    from paper_1801_01037_gb300 import build as sv_build
-    sv_build.build()
-    from paper_1801_01037_gb300 import _binding as B
-    B.load()
-    torch.cuda.init()
-    sweep = []
-    for rate in [float(x) for x in args.served_rates.split(",")]:
-        stream = C.served_stream(args.served_count, rate, seed=1005)
-        srv = B.sv_server_create(150 * 10 ** 9, 512)
-        tickets, arrival, done_at = [], {}, {}
-        lock = threading.Lock()
-        finished = threading.Event()
+    stream = C.served_stream(count, rate, seed=1005)
+    srv = B.sv_server_create(budget, max_active)
+    tickets, arrival, done_at = [], {}, {}
+    lock = threading.Lock()
+    finished = threading.Event()
 
-        def poller():
-            while not finished.is_set() or len(done_at) < len(stream):
-                with lock:
-                    pending = [t for t in tickets if t not in done_at]
-                for t in pending:
-                    d, h = B.sv_poll(srv, t)
-                    if d:
-                        done_at[t] = time.perf_counter()
-                        B.sv_destroy(h)
-                if len(done_at) == len(stream):
-                    break
-                time.sleep(0.0002)
+    def poller():
+        while not finished.is_set() or len(done_at) < len(stream):
+            with lock:
+                pending = [t for t in tickets if t not in done_at]
+            for t in pending:
+                d, h = B.sv_poll(srv, t)
+                if d:
+                    done_at[t] = time.perf_counter()
+                    B.sv_destroy(h)
+            if len(done_at) == len(stream):
+                break
+            time.sleep(0.0002)
 
+    try:
         th = threading.Thread(target=poller)
         th.start()
         t0 = time.perf_counter()
@@ -701,12 +779,26 @@ def run_served(args):
                 arrival[t] = t0 + at
         finished.set()
         th.join()
-        t_end = max(done_at.values())
-        lat = np.array([(done_at[t] - arrival[t]) * 1e3 for t in tickets])
+        stats = B.sv_server_get_stats(srv)
+    finally:
         B.sv_server_destroy(srv)
-        sweep.append({"rate_per_s": rate, "requests": len(stream), "circuits_per_s": len(stream) / (t_end - t0),
-                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                      "mean_ms": float(lat.mean())})
+    t_end = max(done_at.values())
+    lat = np.array([(done_at[t] - arrival[t]) * 1e3 for t in tickets])
+    return {"rate_per_s": rate, "requests": len(stream), "circuits_per_s": len(stream) / (t_end - t0),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "rounds": stats["rounds"], "max_round_chunks": stats["max_round_chunks"]}
+
+
+def run_served(args):
+    """Poisson arrivals through the serving loop (150 GB budget), complex64; per rate: circuits/s and
+    latency percentiles."""
+    import torch
+    from paper_1801_01037_gb300 import build as sv_build
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    B.load()
+    torch.cuda.init()
+    sweep = [served_measure(B, float(x), args.served_count) for x in args.served_rates.split(",")]
     print(json.dumps({"metric": "served circuits/s and p50/p99 latency (complex64, 150 GB budget, continuous batching)",
                       "workload": "Poisson arrivals; each request a random circuit with n log-uniform in [12, 28], "
                                   "10-30 layers, seed 1005", "sweep": sweep}), flush=True)

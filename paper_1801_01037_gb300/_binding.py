@@ -52,8 +52,13 @@ EXPORTED = [
     "sv_get_info", "sv_get_layout", "sv_canonicalize", "sv_apply_gate", "sv_apply_gate2q", "sv_apply_swap", "sv_apply_circuit",
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_run_batch_k", "sv_server_create", "sv_server_destroy",
-    "sv_submit", "sv_poll", "sv_last_error", "sv_version",
+    "sv_submit", "sv_poll", "sv_last_error", "sv_version", "sv_last_batch_stats", "sv_server_pause",
+    "sv_server_get_stats",
 ]
+
+BATCH_STATS_FIELDS = ["rounds", "mixed_rounds", "max_round_chunks", "total_chunks"]
+SERVER_STATS_FIELDS = ["submitted", "admitted", "completed", "failed", "rounds", "mixed_rounds", "max_round_chunks",
+                       "active", "pending", "budget_used"]
 
 
 class SvError(RuntimeError):
@@ -111,6 +116,9 @@ def load(path: str | None = None):
         "sv_server_destroy": [P],
         "sv_submit": [P, i, i, P, sz, ctypes.POINTER(u64)],
         "sv_poll": [P, u64, ctypes.POINTER(i), PP],
+        "sv_last_batch_stats": [P],
+        "sv_server_pause": [P, i],
+        "sv_server_get_stats": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -361,6 +369,23 @@ def sv_poll(srv: int, ticket: int):
     d, r = ctypes.c_int(), ctypes.c_void_p()
     _check(load().sv_poll(srv, ticket, ctypes.byref(d), ctypes.byref(r)))
     return bool(d.value), r.value
+
+
+def sv_last_batch_stats() -> dict:
+    """Statistics of this thread's last sv_run_batch call (sv_batch_stats)."""
+    v = (ctypes.c_uint64 * len(BATCH_STATS_FIELDS))()
+    _check(load().sv_last_batch_stats(ctypes.cast(v, ctypes.c_void_p)))
+    return dict(zip(BATCH_STATS_FIELDS, list(v)))
+
+
+def sv_server_pause(srv: int, paused: bool) -> None:
+    _check(load().sv_server_pause(srv, 1 if paused else 0))
+
+
+def sv_server_get_stats(srv: int) -> dict:
+    v = (ctypes.c_uint64 * len(SERVER_STATS_FIELDS))()
+    _check(load().sv_server_get_stats(srv, ctypes.cast(v, ctypes.c_void_p)))
+    return dict(zip(SERVER_STATS_FIELDS, list(v)))
 
 
 def sv_last_error() -> str:

@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libsv.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["sv_fused.cu", "sv_kernels.cu", "sv_noalloc.cu", "sv_api.cpp", "sv_readout.cpp", "sv_plan.cpp",
-           "sv_batch.cpp"]
+           "sv_block.cpp", "sv_batch.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

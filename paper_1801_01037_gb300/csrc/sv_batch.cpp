@@ -42,6 +42,8 @@ void plan_fresh(sv_state *s, const sv_gate *g, size_t ng, Plan &P) {
   make_plan(s->n, cfg, s->perm, g, ng, P);
 }
 
+thread_local sv_batch_stats t_batch_stats{};
+
 // Grow-only device buffer.
 struct DevBuf {
   void *p = nullptr;
@@ -57,6 +59,12 @@ struct DevBuf {
 };
 
 } // namespace
+
+extern "C" sv_status sv_last_batch_stats(sv_batch_stats *out) {
+  if (!out) return set_error(SV_ERR_ARG, "NULL argument");
+  *out = t_batch_stats;
+  return SV_OK;
+}
 
 extern "C" sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
                                   const size_t *ngates, void *stream, sv_state **out) {
@@ -174,13 +182,58 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ds.p, starts.data(), starts.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   const int mode = default_mode(dtype);
-  for (size_t r = 0; r < rounds.size() && e == cudaSuccess; ++r) {
-    const Round &R = rounds[r];
-    e = launch_fused_batch((const PassDesc *)dd.p + R.desc_off, (const uint64_t *)ds.p + R.start_off, R.npass, R.total,
-                           mode, R.kmax, st, kDefaultF64Share, (FusedSched *)dsched.p);
+  sv_batch_stats bs{};
+  // Every round's launch is queued without a host wait in between (each round's passes depend only on the
+  // previous round, which the stream orders).  With more than one round the launches are captured once into
+  // a CUDA graph on a private stream and the graph is launched on `st`; if capture is not possible the
+  // rounds are launched directly.
+  auto enqueue_rounds = [&](cudaStream_t q) {
+    cudaError_t err = cudaSuccess;
+    bs = sv_batch_stats{};
+    for (size_t r = 0; r < rounds.size() && err == cudaSuccess; ++r) {
+      const Round &R = rounds[r];
+      int mixed = 0;
+      err = launch_fused_batch((const PassDesc *)dd.p + R.desc_off, (const uint64_t *)ds.p + R.start_off, R.npass,
+                               R.total, mode, R.kmax, q, kDefaultF64Share, (FusedSched *)dsched.p, &mixed);
+      ++bs.rounds;
+      bs.mixed_rounds += (uint64_t)mixed;
+      bs.max_round_chunks = std::max<uint64_t>(bs.max_round_chunks, R.total);
+      bs.total_chunks += R.total;
+    }
+    return err;
+  };
+  bool launched = false;
+  if (e == cudaSuccess && rounds.size() > 1) {
+    // Shared-memory grants are raised outside the capture.
+    for (const Round &R : rounds)
+      if ((e = prepare_fused_batch(mode, R.kmax)) != cudaSuccess) break;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
+      if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const cudaError_t le = enqueue_rounds(cap);
+        const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        if (le == cudaSuccess && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+          // the uploads above were queued on `st`; the graph runs after them on the same stream
+          e = cudaGraphLaunch(exec, st);
+          launched = true;
+        }
+      }
+      cudaGetLastError();  // a failed capture leaves its error here; the direct path below reports its own
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
+    }
+    // The descriptor buffers are freed on return, so wait for the launches that read them (a graph exec may be
+    // destroyed as soon as it is launched).
+    if (launched && e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
   }
-  // The descriptor buffers are freed on return, so wait for the launches that read them.
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!launched && e == cudaSuccess) {
+    e = enqueue_rounds(st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  t_batch_stats = bs;
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "batched passes"));
   for (int i = 0; i < count; ++i) {
     states[i]->st_passes = (int)plans[i].passes.size();
@@ -194,6 +247,32 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
 // =========================================================================================================
 // Serving loop
 // =========================================================================================================
+namespace {
+
+// Host-side check of a pass descriptor before it is handed to the batched kernel: every field the kernel
+// indexes with must lie in range.  A descriptor that fails is never launched.
+bool pass_is_sane(const PassDesc &d, int n) {
+  if (!d.psi || d.n != n || d.k < 1 || d.k > kMaxChunkQubits || d.k > n || d.c < 0 || d.c > d.k) return false;
+  if (d.ngates < 0 || (d.ngates > 0 && !d.gates)) return false;
+  uint64_t mask = 0;
+  for (int j = 0; j < d.k; ++j) {
+    const int q = d.qpos[j];
+    if (q < 0 || q >= n || (j > 0 && q <= d.qpos[j - 1]) || (j < d.c && q != j)) return false;
+    mask |= 1ull << q;
+  }
+  return mask == d.qmask;
+}
+
+// Test hooks (host only; the GPU never sees the bad data): the ticket named by SV_FAULT_POISON_TICKET has its
+// gate records overwritten in the queue before admission, the one named by SV_FAULT_CORRUPT_DESC_TICKET has
+// its first pass descriptor corrupted before its first round.
+uint64_t env_ticket(const char *name) {
+  const char *v = std::getenv(name);
+  return v ? (uint64_t)std::strtoull(v, nullptr, 10) : 0;
+}
+
+} // namespace
+
 struct sv_server {
   struct Request {
     uint64_t ticket;
@@ -202,158 +281,300 @@ struct sv_server {
     std::vector<sv_gate> gates;
   };
   struct Active {
-    uint64_t ticket;
-    sv_state *st;
+    uint64_t ticket = 0;
+    sv_state *st = nullptr;
     Plan plan;
-    void *d_gates;   // device blob: the plan's gates
-    size_t next;
-    size_t bytes;
+    std::vector<unsigned char> blob;  // host copy of the gate blob (the source of its upload)
+    void *d_gates = nullptr;          // device blob (stream-ordered allocation on the server stream)
+    size_t launched = 0;              // passes queued so far
+    int inflight = 0;                 // queued rounds not yet retired that hold one of its passes
+    size_t bytes = 0;
+    int mode = 0;
+    int err = SV_OK;                  // set when the request failed; it leaves once `inflight` is 0
+    std::string why;
   };
+  // One queued round: host/device descriptor buffers, the event that marks its end, its members.
+  struct Slot {
+    PassDesc *h_desc = nullptr;
+    uint64_t *h_start = nullptr;
+    size_t cap = 0;
+    DevBuf d_desc, d_start;
+    cudaEvent_t ev = nullptr;
+    std::vector<Active *> members;
+    bool busy = false;
+  };
+  static constexpr int kSlots = 4;
+
   size_t budget = 0, used = 0;
   int max_active = 0;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request> pending;
-  std::vector<Active> active;
   std::unordered_map<uint64_t, std::pair<sv_state *, size_t>> done;
   std::unordered_map<uint64_t, std::pair<int, std::string>> failed;
   std::unordered_set<uint64_t> live;
   uint64_t next_ticket = 1;
-  bool stop = false;
+  bool stop = false, paused = false;
+  sv_server_stats stats{};
   std::thread th;
   cudaStream_t stream = nullptr;
-  DevBuf d_desc, d_start, d_sched;
-  PassDesc *h_desc = nullptr;
-  uint64_t *h_start = nullptr;
-  size_t h_cap = 0;
+  // loop-thread state (no lock needed)
+  std::vector<Active *> active;
+  Slot slots[kSlots];
+  std::deque<int> queued;  // slot indices in launch order
+  DevBuf d_sched;
+  uint64_t poison = 0, corrupt = 0;
 
-  void fail_request(uint64_t ticket, int code, const std::string &msg) {
-    failed[ticket] = {code, msg};
-  }
-
-  // Move admissible pending requests into the active set (called with mu held).
-  void admit() {
-    while (!pending.empty() && (int)active.size() < max_active) {
-      Request &r = pending.front();
-      const size_t bytes = amp_bytes(r.dtype) << r.n;
-      if (used + bytes > budget) break;
-      Active a{r.ticket, nullptr, Plan(), nullptr, 0, bytes};
-      int rc = alloc_state(r.n, r.dtype, stream, &a.st, false);
-      if (rc != SV_OK) {
-        if (rc == SV_ERR_OOM && !active.empty()) break;  // wait for memory to free up
-        fail_request(r.ticket, rc, sv_last_error());
-        pending.pop_front();
-        continue;
-      }
-      plan_fresh(a.st, r.gates.data(), r.gates.size(), a.plan);
-      if (plan_blob_bytes(a.plan) > 0) {
-        const size_t gb = plan_blob_bytes(a.plan);
-        std::vector<unsigned char> blob(gb);
-        plan_blob_fill(a.plan, blob.data());
-        if (cudaMalloc(&a.d_gates, gb) != cudaSuccess ||
-            cudaMemcpyAsync(a.d_gates, blob.data(), gb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-            cudaStreamSynchronize(stream) != cudaSuccess) {
-          cudaGetLastError();
-          if (a.d_gates) cudaFree(a.d_gates);
-          sv_destroy(a.st);
-          fail_request(r.ticket, SV_ERR_OOM, "gate buffer allocation failed");
-          pending.pop_front();
-          continue;
-        }
-      }
-      used += bytes;
-      active.push_back(std::move(a));
-      pending.pop_front();
+  ~sv_server() {
+    for (Slot &sl : slots) {
+      if (sl.h_desc) cudaFreeHost(sl.h_desc);
+      if (sl.h_start) cudaFreeHost(sl.h_start);
+      if (sl.ev) cudaEventDestroy(sl.ev);
     }
   }
 
-  int ensure_host(size_t m) {
-    if (m <= h_cap) return SV_OK;
-    if (h_desc) cudaFreeHost(h_desc);
-    if (h_start) cudaFreeHost(h_start);
-    h_desc = nullptr;
-    h_start = nullptr;
-    h_cap = 0;
-    if (cudaMallocHost(&h_desc, m * sizeof(PassDesc)) != cudaSuccess ||
-        cudaMallocHost(&h_start, (m + 1) * sizeof(uint64_t)) != cudaSuccess)
+  // Called with mu held.
+  void record_failure(uint64_t ticket, int code, const std::string &msg) {
+    failed[ticket] = {code, msg};
+    ++stats.failed;
+  }
+
+  // Release an Active that left (finished or failed); its state goes to `done` or is destroyed.
+  void retire_active(Active *a) {
+    if (a->d_gates) cudaFreeAsync(a->d_gates, stream);
+    a->d_gates = nullptr;
+    if (a->err != SV_OK) {
+      sv_destroy(a->st);  // waits for the server stream: outside the lock
+      a->st = nullptr;
+    } else {
+      a->st->st_passes = (int)a->plan.passes.size();
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (a->err == SV_OK) {
+      done[a->ticket] = {a->st, a->bytes};
+      ++stats.completed;
+    } else {
+      record_failure(a->ticket, a->err, a->why);
+      used -= a->bytes;
+    }
+    --stats.active;
+    delete a;
+  }
+
+  // Admission of one popped request, outside the lock: state allocation, planning, gate upload.
+  // Returns false if it must wait for memory (the request is put back in front of the queue).
+  bool admit_one(Request &r) {
+    const size_t bytes = amp_bytes(r.dtype) << r.n;
+    std::string why;
+    size_t bad = 0;
+    int rc = validate_records(r.gates.data(), r.gates.size(), r.n, why, bad);
+    if (rc != SV_OK) {
+      std::lock_guard<std::mutex> lk(mu);
+      used -= bytes;
+      record_failure(r.ticket, rc, "gate " + std::to_string(bad) + " failed validation at admission: " + why);
+      return true;
+    }
+    Active *a = new Active();
+    a->ticket = r.ticket;
+    a->bytes = bytes;
+    a->mode = default_mode(r.dtype);
+    rc = alloc_state(r.n, r.dtype, stream, &a->st, false);
+    if (rc != SV_OK) {
+      const std::string msg = sv_last_error();
+      delete a;
+      std::lock_guard<std::mutex> lk(mu);
+      used -= bytes;
+      if (rc == SV_ERR_OOM && !active.empty()) {  // wait for running requests to free memory
+        pending.push_front(std::move(r));
+        return false;
+      }
+      record_failure(r.ticket, rc, msg);
+      return true;
+    }
+    plan_fresh(a->st, r.gates.data(), r.gates.size(), a->plan);
+    const size_t gb = plan_blob_bytes(a->plan);
+    cudaError_t e = cudaSuccess;
+    if (gb > 0) {
+      a->blob.resize(gb);
+      plan_blob_fill(a->plan, a->blob.data());
+      e = cudaMallocAsync(&a->d_gates, gb, stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(a->d_gates, a->blob.data(), gb, cudaMemcpyHostToDevice, stream);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (a->d_gates) cudaFreeAsync(a->d_gates, stream);
+      sv_destroy(a->st);
+      delete a;
+      std::lock_guard<std::mutex> lk(mu);
+      used -= bytes;
+      record_failure(r.ticket, SV_ERR_OOM, "gate buffer allocation failed");
+      return true;
+    }
+    if (r.ticket == corrupt && !a->plan.passes.empty()) a->plan.passes[0].k = 40;  // test hook (host only)
+    active.push_back(a);
+    std::lock_guard<std::mutex> lk(mu);
+    ++stats.admitted;
+    ++stats.active;
+    return true;
+  }
+
+  int ensure_slot(Slot &sl, size_t m) {
+    if (!sl.ev && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) return SV_ERR_CUDA;
+    if (m > sl.cap) {
+      if (sl.h_desc) cudaFreeHost(sl.h_desc);
+      if (sl.h_start) cudaFreeHost(sl.h_start);
+      sl.h_desc = nullptr;
+      sl.h_start = nullptr;
+      sl.cap = 0;
+      const size_t c = std::max<size_t>(m, 64);
+      if (cudaMallocHost(&sl.h_desc, c * sizeof(PassDesc)) != cudaSuccess ||
+          cudaMallocHost(&sl.h_start, (c + 1) * sizeof(uint64_t)) != cudaSuccess)
+        return SV_ERR_OOM;
+      sl.cap = c;
+    }
+    if (sl.d_desc.ensure(sl.cap * sizeof(PassDesc), stream) != SV_OK ||
+        sl.d_start.ensure((sl.cap + 1) * sizeof(uint64_t), stream) != SV_OK)
       return SV_ERR_OOM;
-    h_cap = m;
     return SV_OK;
   }
 
+  // Queue one round of `mode`: the next pass of every active request of that mode with passes left.
+  // Returns true if a round was queued.
+  bool launch_round(int mode) {
+    int si = -1;
+    for (int i = 0; i < kSlots; ++i)
+      if (!slots[i].busy) { si = i; break; }
+    if (si < 0) return false;
+    Slot &sl = slots[si];
+    std::vector<Active *> members;
+    for (Active *a : active)
+      if (a->mode == mode && a->err == SV_OK && a->launched < a->plan.passes.size()) members.push_back(a);
+    if (members.empty()) return false;
+    if (ensure_slot(sl, members.size()) != SV_OK || d_sched.ensure(sizeof(FusedSched), stream) != SV_OK) {
+      for (Active *a : members) { a->err = SV_ERR_OOM; a->why = "round descriptor allocation failed"; }
+      return false;
+    }
+    uint64_t total = 0;
+    int kmax = 0;
+    size_t m = 0;
+    sl.members.clear();
+    for (Active *a : members) {
+      PassDesc d = a->plan.passes[a->launched];
+      d.psi = a->st->psi;
+      plan_pass_pointers(a->plan, (int)a->launched, a->d_gates, d);
+      if (!pass_is_sane(d, a->st->n)) {
+        a->err = SV_ERR_ARG;
+        a->why = "pass " + std::to_string(a->launched) + " failed the host's descriptor check; not launched";
+        continue;
+      }
+      sl.h_desc[m] = d;
+      sl.h_start[m] = total;
+      total += 1ull << (d.n - d.k);
+      kmax = std::max(kmax, d.k);
+      sl.members.push_back(a);
+      ++m;
+    }
+    if (m == 0) return false;
+    sl.h_start[m] = total;
+    cudaError_t e = cudaMemcpyAsync(sl.d_desc.p, sl.h_desc, m * sizeof(PassDesc), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sl.d_start.p, sl.h_start, (m + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, stream);
+    int mixed = 0;
+    if (e == cudaSuccess)
+      e = launch_fused_batch((const PassDesc *)sl.d_desc.p, (const uint64_t *)sl.d_start.p, (int)m, total, mode, kmax,
+                             stream, kDefaultF64Share, (FusedSched *)d_sched.p, &mixed);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      const std::string msg = std::string("serving round: ") + cudaGetErrorString(e);
+      for (Active *a : sl.members) { a->err = SV_ERR_CUDA; a->why = msg; }
+      sl.members.clear();
+      return false;
+    }
+    for (Active *a : sl.members) {
+      ++a->launched;
+      ++a->inflight;
+    }
+    sl.busy = true;
+    queued.push_back(si);
+    std::lock_guard<std::mutex> lk(mu);
+    ++stats.rounds;
+    stats.mixed_rounds += (uint64_t)mixed;
+    stats.max_round_chunks = std::max<uint64_t>(stats.max_round_chunks, total);
+    return true;
+  }
+
+  // Wait for the oldest queued round and retire the requests whose last pass it held.
+  void retire_oldest() {
+    const int si = queued.front();
+    queued.pop_front();
+    Slot &sl = slots[si];
+    const cudaError_t e = cudaEventSynchronize(sl.ev);
+    for (Active *a : sl.members) {
+      --a->inflight;
+      if (e != cudaSuccess && a->err == SV_OK) {
+        a->err = SV_ERR_CUDA;
+        a->why = std::string("serving round: ") + cudaGetErrorString(e);
+      }
+    }
+    sl.members.clear();
+    sl.busy = false;
+  }
+
+  // Requests that finished (all passes queued and retired) or failed (nothing of theirs still queued) leave.
+  void sweep_finished() {
+    std::vector<Active *> keep;
+    for (Active *a : active) {
+      const bool finished = a->err == SV_OK && a->launched == a->plan.passes.size() && a->inflight == 0;
+      const bool dead = a->err != SV_OK && a->inflight == 0;
+      if (finished || dead) retire_active(a);
+      else keep.push_back(a);
+    }
+    active.swap(keep);
+  }
+
   void loop() {
+    poison = env_ticket("SV_FAULT_POISON_TICKET");
+    corrupt = env_ticket("SV_FAULT_CORRUPT_DESC_TICKET");
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
-      admit();
-      if (active.empty()) {
-        if (stop) break;
-        cv.wait_for(lk, std::chrono::milliseconds(2));
-        continue;
+      // Admission: pick requests under the lock (reserving their budget), do the work outside it.
+      std::vector<Request> take;
+      while (!paused && !pending.empty() && active.size() + take.size() < (size_t)max_active) {
+        Request &r = pending.front();
+        const size_t bytes = amp_bytes(r.dtype) << r.n;
+        if (used + bytes > budget) break;
+        used += bytes;
+        if (r.ticket == poison && !r.gates.empty()) r.gates[0].target = 1000;  // test hook (host only)
+        take.push_back(std::move(r));
+        pending.pop_front();
       }
-      // One round: the next pass of every active request of one dtype, in one launch.
-      const int mode = default_mode(active[0].st->dtype);
-      std::vector<size_t> in_round;
-      for (size_t i = 0; i < active.size(); ++i)
-        if (default_mode(active[i].st->dtype) == mode) in_round.push_back(i);
-      const size_t m = active.size();
-      const size_t used_m = in_round.size();
-      if (ensure_host(used_m) != SV_OK || d_desc.ensure(used_m * sizeof(PassDesc), stream) != SV_OK ||
-          d_start.ensure((used_m + 1) * sizeof(uint64_t), stream) != SV_OK ||
-          d_sched.ensure(sizeof(FusedSched), stream) != SV_OK) {
-        for (Active &a : active) {
-          fail_request(a.ticket, SV_ERR_OOM, "round descriptor allocation failed");
-          if (a.d_gates) cudaFree(a.d_gates);
-          sv_destroy(a.st);
-          used -= a.bytes;
-        }
-        active.clear();
-        continue;
-      }
-      uint64_t total = 0;
-      int kmax = 0;
-      for (size_t j = 0; j < used_m; ++j) {
-        Active &a = active[in_round[j]];
-        PassDesc d = a.plan.passes[a.next];
-        d.psi = a.st->psi;
-        plan_pass_pointers(a.plan, (int)a.next, a.d_gates, d);
-        h_desc[j] = d;
-        h_start[j] = total;
-        total += 1ull << (d.n - d.k);
-        kmax = std::max(kmax, d.k);
-      }
-      h_start[used_m] = total;
+      stats.pending = pending.size();
+      const bool stopping = stop;
       lk.unlock();
-      cudaError_t e = cudaMemcpyAsync(d_desc.p, h_desc, used_m * sizeof(PassDesc), cudaMemcpyHostToDevice, stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_start.p, h_start, (used_m + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, stream);
-      if (e == cudaSuccess)
-        e = launch_fused_batch((const PassDesc *)d_desc.p, (const uint64_t *)d_start.p, (int)used_m, total, mode, kmax, stream,
-                               kDefaultF64Share, (FusedSched *)d_sched.p);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      for (size_t i = 0; i < take.size(); ++i)
+        if (!admit_one(take[i])) {
+          // put the rest back in order, behind the one admit_one returned to the front
+          std::lock_guard<std::mutex> g(mu);
+          for (size_t j = take.size(); j-- > i + 1;) {
+            used -= amp_bytes(take[j].dtype) << take[j].n;
+            pending.insert(pending.begin() + 1, std::move(take[j]));
+          }
+          break;
+        }
+      sweep_finished();
+      // One round per dtype with work, while queue slots are free: complex64 and complex128 advance together.
+      bool any = false;
+      for (int mode : {(int)MODE_C64_F32, (int)MODE_C128_DF32})
+        if (queued.size() < (size_t)kSlots) any |= launch_round(mode);
+      // Keep at most two rounds ahead of the host; wait for the oldest when full or when nothing new was queued.
+      if (!queued.empty() && (queued.size() >= 2 || !any)) retire_oldest();
+      sweep_finished();
       lk.lock();
-      std::vector<Active> keep;
-      std::vector<char> in(m, 0);
-      for (size_t i : in_round) in[i] = 1;
-      for (size_t i = 0; i < m; ++i) {
-        Active &a = active[i];
-        if (!in[i]) { keep.push_back(std::move(a)); continue; }
-        if (e != cudaSuccess) {
-          fail_request(a.ticket, SV_ERR_CUDA, std::string("serving round: ") + cudaGetErrorString(e));
-          if (a.d_gates) cudaFree(a.d_gates);
-          sv_destroy(a.st);
-          used -= a.bytes;
-          continue;
-        }
-        ++a.next;
-        if (a.next >= a.plan.passes.size()) {
-          if (a.d_gates) cudaFree(a.d_gates);
-          a.st->st_passes = (int)a.plan.passes.size();
-          done[a.ticket] = {a.st, a.bytes};
-        } else {
-          keep.push_back(std::move(a));
-        }
+      if (active.empty() && queued.empty()) {
+        if (stopping && pending.empty()) break;
+        if (pending.empty() || paused) cv.wait_for(lk, std::chrono::milliseconds(2));
       }
-      active.swap(keep);
     }
   }
 };
@@ -381,14 +602,14 @@ sv_status sv_server_destroy(sv_server *s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    s->paused = false;
+    for (const auto &r : s->pending) s->live.erase(r.ticket);
     s->pending.clear();
   }
   s->cv.notify_all();
   s->th.join();
+  cudaStreamSynchronize(s->stream);
   for (auto &kv : s->done) sv_destroy(kv.second.first);
-  for (auto &a : s->active) { if (a.d_gates) cudaFree(a.d_gates); sv_destroy(a.st); }
-  if (s->h_desc) cudaFreeHost(s->h_desc);
-  if (s->h_start) cudaFreeHost(s->h_start);
   cudaStreamDestroy(s->stream);
   delete s;
   return SV_OK;
@@ -409,6 +630,8 @@ sv_status sv_submit(sv_server *s, int n, sv_dtype dtype, const sv_gate *gates, s
     *ticket = r.ticket;
     s->live.insert(r.ticket);
     s->pending.push_back(std::move(r));
+    ++s->stats.submitted;
+    s->stats.pending = s->pending.size();
   }
   s->cv.notify_all();
   return SV_OK;
@@ -443,6 +666,25 @@ sv_status sv_poll(sv_server *s, uint64_t ticket, int *done, sv_state **result) {
     return SV_OK;
   }
   return set_error(SV_ERR_NOT_FOUND, "unknown ticket");
+}
+
+sv_status sv_server_pause(sv_server *s, int paused) {
+  if (!s) return set_error(SV_ERR_ARG, "NULL argument");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv.notify_all();
+  return SV_OK;
+}
+
+sv_status sv_server_get_stats(sv_server *s, sv_server_stats *out) {
+  if (!s || !out) return set_error(SV_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->pending = s->pending.size();
+  out->budget_used = s->used;
+  return SV_OK;
 }
 
 } // extern "C"

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include "sv_internal.h"
 #include "sv_arith.cuh"
 
@@ -274,6 +275,204 @@ __device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint64_t po
 #pragma unroll
     for (int s = 0; s < (1 << CB); ++s) sm[b1 ^ cube_xoff<CB>(s, soff)] = v[s];
   }
+}
+
+// ---- Dense blocks on the tensor cores (GC_BLOCK) -----------------------------------------------------
+// A block multiplies every row of the chunk (the 16 amplitudes that differ only in the block's 4 chunk bits)
+// by the block's matrix: D = X W^T with X the rows in real form (Re 0..15 | Im 0..15) and W the real form of
+// the 16 x 16 unitary.  X is written to shared memory as bfloat16 planes (A operand), W's planes come from the
+// gate blob (B operand); one thread issues tcgen05.mma (M = 128 rows, N = 32, K = 16 per instruction) into a
+// TMEM accumulator, commits to an mbarrier, and after the bounded wait every thread reads its row of D back
+// with tcgen05.ld and stores the 16 new amplitudes into the chunk.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Shared-memory matrix descriptor of an operand plane: no swizzle, K-major core matrices of 8 rows x 16 bytes,
+// K-adjacent core matrices 128 bytes apart (leading byte offset), 8-row groups 512 bytes apart (stride byte
+// offset), descriptor version 1 (bit 46).  The layout is the one sv_block.cpp writes for W.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), bfloat16 A and B (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBlockK >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+constexpr int kTcRowBytes = kBlockK * 2;          // one row of one plane
+constexpr int kTcTileBytes = 128 * kTcRowBytes;   // 128 rows of one plane
+constexpr uint64_t kTcWaitNs = 2000000000ull;     // bound of one wait for the tensor cores
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+               : "memory");
+}
+
+// Bounded wait for the mbarrier phase with parity `ph`; false if it ran out.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t ph) {
+  const uint32_t a = smem_addr(mbar);
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(a), "r"(ph)
+                 : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > kTcWaitNs) return false;
+  }
+}
+
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tc_load32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Per-CTA state of the tensor-core pass (the same in every thread).
+struct TcCtx {
+  unsigned char *opA;   // A planes: plane-major, rows x kTcRowBytes each
+  unsigned char *opB;   // B planes: kBlockPlaneBytes each
+  uint64_t *mbar;
+  uint32_t tmem;        // TMEM address of this CTA's accumulators (lane 0, first column)
+  uint32_t phase;       // parity of the next mbarrier phase
+  int ok;               // 0 once a wait ran out: later blocks are skipped
+  unsigned *err;        // global error word
+};
+
+// Row r's base slot and the 16 slot offsets of its amplitudes (slot maps are linear over GF(2)).
+template <int MODE>
+__device__ __forceinline__ void tc_row_slots(uint32_t r, const int (&pb)[kBlockBits], uint32_t &b0) {
+  uint32_t bidx = r;
+#pragma unroll
+  for (int j = 0; j < kBlockBits; ++j) bidx = ins0(bidx, pb[j]);
+  b0 = slot<MODE>(bidx);
+}
+
+// 16-byte store of eight bfloat16 values (four packed pairs).
+__device__ __forceinline__ void st_planes(unsigned char *dst, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  *reinterpret_cast<uint4 *>(dst) = make_uint4(w0, w1, w2, w3);
+}
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// Complex64 block: rows split into three bfloat16 planes (x = x0 + x1 + x2, 24 bits), six products.
+__device__ __forceinline__ void tc_block_c64(const DevGate &h, float2 *sm, int k, TcCtx &tc) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t R = 1u << (k - kBlockBits);
+  const unsigned char *planes = reinterpret_cast<const unsigned char *>(&h) + h.gmask;
+  // B planes (the block's matrix) into shared memory.
+  for (uint32_t u = tid; u < (uint32_t)(kBlockSplitsC64 * kBlockPlaneBytes / 16); u += kFusedThreads)
+    cp_async16(tc.opB + 16u * u, planes + 16u * u);
+  int pb[kBlockBits];
+  uint32_t xo[kBlockDim];
+#pragma unroll
+  for (int j = 0; j < kBlockBits; ++j) pb[j] = (int)((h.cmask >> (8 * j)) & 0xffu);
+#pragma unroll
+  for (int s = 0; s < kBlockDim; ++s) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int j = 0; j < kBlockBits; ++j)
+      if (s & (1 << j)) x ^= slot<MODE_C64_F32>(1u << pb[j]);
+    xo[s] = x;
+  }
+  // A planes: row r at (r / 8) * 512 + (r % 8) * 16 in each 128-row tile; K groups of 8 columns 128 bytes apart.
+  for (uint32_t r = tid; r < R; r += kFusedThreads) {
+    uint32_t b0;
+    tc_row_slots<MODE_C64_F32>(r, pb, b0);
+    float re[kBlockDim], im[kBlockDim];
+#pragma unroll
+    for (int s = 0; s < kBlockDim; ++s) {
+      const float2 v = sm[b0 ^ xo[s]];
+      re[s] = v.x;
+      im[s] = v.y;
+    }
+    unsigned char *row = tc.opA + (r / 8) * 512 + (r % 8) * 16;
+#pragma unroll
+    for (int pl = 0; pl < kBlockSplitsC64; ++pl) {
+      uint32_t w[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        // pairs (2q, 2q + 1): Re for q < 8 ... written as K columns 0..15 (Re) and 16..31 (Im)
+        const __nv_bfloat162 hr = __floats2bfloat162_rn(re[2 * q], re[2 * q + 1]);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(im[2 * q], im[2 * q + 1]);
+        w[q] = bf2_bits(hr);
+        w[8 + q] = bf2_bits(hi);
+        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
+        re[2 * q] -= fr.x;
+        re[2 * q + 1] -= fr.y;
+        im[2 * q] -= fi.x;
+        im[2 * q + 1] -= fi.y;
+      }
+      unsigned char *dst = row + (size_t)pl * R * kTcRowBytes;
+      st_planes(dst + 0 * 128, w[0], w[1], w[2], w[3]);
+      st_planes(dst + 1 * 128, w[4], w[5], w[6], w[7]);
+      st_planes(dst + 2 * 128, w[8], w[9], w[10], w[11]);
+      st_planes(dst + 3 * 128, w[12], w[13], w[14], w[15]);
+    }
+  }
+  cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  const uint32_t ntiles = R / 128;
+  if (tid == 0 && tc.ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t a0 = smem_addr(tc.opA), b0 = smem_addr(tc.opB);
+    for (uint32_t t = 0; t < ntiles; ++t) {
+      const uint32_t d = tc.tmem + t * kBlockK;
+      uint32_t acc = 0;
+      // products x_i w_j with i + j <= 2 (i: A plane, j: B plane)
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr) {
+        const int i = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+        const int j = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+#pragma unroll
+        for (int ks = 0; ks < kBlockK / 16; ++ks) {
+          const uint32_t aa = a0 + (uint32_t)i * R * kTcRowBytes + t * kTcTileBytes + (uint32_t)ks * 256;
+          const uint32_t bb = b0 + (uint32_t)j * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256;
+          tc_mma(d, tc_desc(aa), tc_desc(bb), acc);
+          acc = 1;
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(tc.mbar))
+                 : "memory");
+  }
+  // Every thread waits for the MMAs (bounded); a wait that ran out stops the tensor-core work of this CTA.
+  int ok = tc.ok ? (tc_wait(tc.mbar, tc.phase) ? 1 : 0) : 0;
+  ok = __syncthreads_and(ok);
+  if (tc.ok) tc.phase ^= 1u;
+  if (!ok && tc.ok && tid == 0) atomicOr(tc.err, 1u);
+  tc.ok = ok;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // Read back: warp w reads TMEM lanes 32 (w % 4) ..; warp group g = w / 4 takes tiles g, g + 2, ...
+  const uint32_t lane = tid & 127u, group = tid >> 7;
+  for (uint32_t t = group; t < ntiles; t += kFusedThreads / 128) {
+    float dv[32];
+    tc_load32(tc.tmem + ((tid & 96u) << 16) + t * kBlockK, dv);
+    if (ok) {
+      uint32_t b0;
+      tc_row_slots<MODE_C64_F32>(t * 128 + lane, pb, b0);
+#pragma unroll
+      for (int s = 0; s < kBlockDim; ++s) sm[b0 ^ xo[s]] = make_float2(dv[s], dv[kBlockDim + s]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
 }
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
@@ -593,11 +792,20 @@ cudaError_t fused_launch(const PassDesc &p, cudaStream_t st) {
 }
 
 template <int MODE>
+std::atomic<int> *batch_granted() {
+  static std::atomic<int> granted[64] = {};
+  return granted;
+}
+std::atomic<int> *batch_mixed_granted() {
+  static std::atomic<int> granted[64] = {};
+  return granted;
+}
+
+template <int MODE>
 cudaError_t fused_batch_launch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
                                int kmax, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(kmax);
-  static std::atomic<int> granted[64] = {};
-  cudaError_t e = ensure_smem((const void *)k_fused_batch<MODE>, smem, granted);
+  cudaError_t e = ensure_smem((const void *)k_fused_batch<MODE>, smem, batch_granted<MODE>());
   if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_batch<MODE>, kFusedThreads, smem);
@@ -627,7 +835,7 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
     const uint64_t grid = (uint64_t)sms() * occ;
     // Worth it only with several chunks per CTA and at least two CTAs per SM.
     if (occ >= 2 && nchunks >= 4 * grid) {
-      cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(FusedSched), st);
+      cudaError_t e = cudaMemsetAsync(sched, 0, kSchedResetBytes, st);
       if (e != cudaSuccess) return e;
       k_fused_mixed<<<(unsigned)grid, kFusedThreads, smem, st>>>(p, nchunks, f64_share, sched);
       return cudaGetLastError();
@@ -640,22 +848,40 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
   }
 }
 
+cudaError_t prepare_fused_batch(int mode, int kmax) {
+  cudaError_t e;
+  switch (mode) {
+    case MODE_C64_F32:
+      return ensure_smem((const void *)k_fused_batch<MODE_C64_F32>, smem_bytes<MODE_C64_F32>(kmax),
+                         batch_granted<MODE_C64_F32>());
+    case MODE_C128_F64:
+      return ensure_smem((const void *)k_fused_batch<MODE_C128_F64>, smem_bytes<MODE_C128_F64>(kmax),
+                         batch_granted<MODE_C128_F64>());
+    default:
+      e = ensure_smem((const void *)k_fused_batch<MODE_C128_DF32>, smem_bytes<MODE_C128_DF32>(kmax),
+                      batch_granted<MODE_C128_DF32>());
+      if (e != cudaSuccess) return e;
+      return ensure_smem((const void *)k_fused_batch_mixed, smem_bytes<MODE_C128_DF32>(kmax), batch_mixed_granted());
+  }
+}
+
 cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
-                               int mode, int kmax, cudaStream_t st, int f64_share, FusedSched *sched) {
+                               int mode, int kmax, cudaStream_t st, int f64_share, FusedSched *sched, int *used_mixed) {
+  if (used_mixed) *used_mixed = 0;
   if (total == 0 || npass == 0) return cudaSuccess;
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
     const int smem = smem_bytes<MODE_C128_DF32>(kmax);
-    static std::atomic<int> granted[64] = {};
-    cudaError_t e = ensure_smem((const void *)k_fused_batch_mixed, smem, granted);
+    cudaError_t e = ensure_smem((const void *)k_fused_batch_mixed, smem, batch_mixed_granted());
     if (e != cudaSuccess) return e;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_batch_mixed, kFusedThreads, smem);
     if (occ < 1) occ = 1;
     const uint64_t grid = (uint64_t)sms() * occ;
     if (occ >= 2 && total >= 4 * grid) {
-      if ((e = cudaMemsetAsync(sched, 0, sizeof(FusedSched), st)) != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(sched, 0, kSchedResetBytes, st)) != cudaSuccess) return e;
       k_fused_batch_mixed<<<(unsigned)grid, kFusedThreads, smem, st>>>(d_passes, d_chunk_start, npass, total, kmax,
                                                                         f64_share, sched);
+      if (used_mixed) *used_mixed = 1;
       return cudaGetLastError();
     }
   }

@@ -27,7 +27,28 @@ enum GateClass : uint32_t {
   GC_DENSE4 = 6,    // dense two-qubit gate: this record holds row 0 of V, `target` the chunk bit of b0 and
                     //   `tmask` the chunk bit of b1 (both always inside the chunk); then three GC_ROW records
   GC_ROW = 7,       // rows 1..3 of the GC_DENSE4 record before it
+  GC_BLOCK = 8,     // not a gate: a dense unitary on kBlockBits chunk-local bits applied with tcgen05 MMAs
+                    //   (see below); `target` = number of source gates it replaces
 };
+
+// Dense block.  A header DevGate with cls = GC_BLOCK stands for the product of a run of gates whose qubits all
+// lie in kBlockBits chunk-local bits (packed one per byte in `cmask`, ascending).  Every row of the chunk (the
+// 2^kBlockBits amplitudes that differ only in those bits) is multiplied by the block's matrix in its real
+// form W (kBlockK x kBlockK: outputs Re 0..15, Im 0..15 by inputs Re 0..15, Im 0..15): D = X W^T, one
+// tcgen05.mma chain per 128 rows, A = the rows (shared memory, bfloat16 planes), B = W (bfloat16 planes).
+// `gmask` = byte offset from the header to its operand planes in the device gate blob (kBlockPlaneBytes per
+// plane, in the kernel's shared-memory layout).  complex64: three planes w = w0 + w1 + w2; the rows are split
+// the same way and the six products with i + j <= 2 are accumulated in FP32 (24 bits of each factor).
+// complex128: six planes of balanced base-256 digits of w * 2^47 against the rows' digits of x * 2^(47 - E)
+// (E: a power of two above the chunk's 2-norm, which the pass's unitaries preserve); the products are exact
+// integers, accumulated per digit level in FP32 (exactly: every partial sum stays below 2^22) and combined
+// in double-float.
+constexpr int kBlockBits = 4;
+constexpr int kBlockDim = 1 << kBlockBits;   // complex amplitudes per row
+constexpr int kBlockK = 2 * kBlockDim;       // reals per row (re | im)
+constexpr int kBlockSplitsC64 = 3;
+constexpr int kBlockDigitsC128 = 6;
+constexpr size_t kBlockPlaneBytes = (size_t)kBlockK * kBlockK * 2;
 
 // Register cube.  Inside a complex64 fused pass, a header DevGate with cls = GC_CUBE says that the next
 // `target` gates act only on the `tmask` (= kCubeBits) chunk-local bits packed one per byte in `cmask`
@@ -70,8 +91,10 @@ struct PassDesc {
   int32_t init;           // 0: read the chunk from HBM; 1: synthesise |init_x> restricted to the chunk
   int32_t permuted;       // 1 if qpos_out differs from qpos
   int8_t src_bit[16];     // permuted: bit j of the local amplitude stored at slot o is bit src_bit[j] of o
+  int32_t nblocks;        // GC_BLOCK records among the gates (> 0: the pass needs the tensor-core kernel)
+  int32_t reserved;
 };
-static_assert(sizeof(PassDesc) == 104, "PassDesc layout");
+static_assert(sizeof(PassDesc) == 112, "PassDesc layout");
 
 // ---------------------------------------------------------------------------------------------------------
 // Kernel launchers (sv_kernels.cu).  All return cudaGetLastError() of the launch.
@@ -87,7 +110,13 @@ constexpr int kSchedSlots = 256;
 struct FusedSched {
   unsigned sm_slot[kSchedSlots];
   unsigned long long next[2];
+  // Error word of the tensor-core pass: non-zero when a bounded wait for the tensor cores ran out (the kernel
+  // then stops applying blocks).  Not cleared by the launches that reset the fields above; the host reads and
+  // clears it (read_tc_error).
+  unsigned tc_err;
+  unsigned pad;
 };
+constexpr size_t kSchedResetBytes = offsetof(FusedSched, tc_err);
 
 cudaError_t launch_sweep(void *psi, int n, int mode, const DevGate &g, cudaStream_t st);
 
@@ -107,6 +136,11 @@ int norm_parts();
 // pmask != 0: sum of (-1)^popcount(k & pmask) |psi_k|^2 over physical k instead (Pauli-Z expectation).
 cudaError_t launch_norm(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
                         uint64_t pmask = 0);
+// The same with an explicit partial count (`parts` blocks in stage 1, any value >= 1; the result's rounding
+// depends on it), e.g. norm_parts_for_sms(SM count of the current device).
+int norm_parts_for_sms(int sms);
+cudaError_t launch_norm_parts(const void *psi, int n, int mode, double *d_partials, double *d_out, cudaStream_t st,
+                              uint64_t pmask, int parts);
 // Sampling: FP64 probability mass of each block of 2^b consecutive logical indices, then one lookup per shot
 // inside its block (d_blk[i] = block, d_resid[i] = mass to skip inside it) -> logical index.
 cudaError_t launch_block_probs(const void *psi, int n, int mode, const int *perm, int b, double *d_out,
@@ -119,9 +153,13 @@ cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cuda
 // of pass p, where chunk_start is an exclusive prefix sum over the passes' chunk counts (device array of
 // npass + 1 entries).  All passes share `mode`; each has its own k <= kmax (shared memory is sized for kmax).
 // f64_share / sched: as for launch_fused (complex128 double-float: that percent of the round's chunks, by
-// their index in the round, run in native FP64 on one CTA per SM).
+// their index in the round, run in native FP64 on one CTA per SM).  *used_mixed (if given) is set to 1 when
+// the round ran in that split kernel (k_fused_batch_mixed), else 0.
+// Raise the shared-memory grants of the batched kernels of `mode` for chunks of up to 2^kmax amplitudes (done
+// by the launcher itself too; call it before a stream capture so that no attribute is set during one).
+cudaError_t prepare_fused_batch(int mode, int kmax);
 cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass,
                                uint64_t total_chunks, int mode, int kmax, cudaStream_t st, int f64_share = 0,
-                               FusedSched *sched = nullptr);
+                               FusedSched *sched = nullptr, int *used_mixed = nullptr);
 
 } // namespace svi

@@ -187,10 +187,25 @@ int validate_records(const sv_gate *g, size_t ngates, int n, std::string &why, s
   return SV_OK;
 }
 
-size_t plan_blob_bytes(const Plan &P) { return P.fused_gates.size() * sizeof(DevGate); }
+// Device blob: the DevGates of every pass, then (128-byte aligned) the operand planes of the dense blocks.
+static size_t gates_bytes_aligned(const Plan &P) {
+  const size_t b = P.fused_gates.size() * sizeof(DevGate);
+  return P.block_data.empty() ? b : (b + 127) & ~(size_t)127;
+}
+
+size_t plan_blob_bytes(const Plan &P) { return gates_bytes_aligned(P) + P.block_data.size(); }
 
 void plan_blob_fill(const Plan &P, void *dst) {
   if (!P.fused_gates.empty()) std::memcpy(dst, P.fused_gates.data(), P.fused_gates.size() * sizeof(DevGate));
+  if (P.block_data.empty()) return;
+  const size_t base = gates_bytes_aligned(P);
+  std::memset((unsigned char *)dst + P.fused_gates.size() * sizeof(DevGate), 0,
+              base - P.fused_gates.size() * sizeof(DevGate));
+  std::memcpy((unsigned char *)dst + base, P.block_data.data(), P.block_data.size());
+  // A block header's gmask becomes the byte distance from the header to its planes.
+  DevGate *g = (DevGate *)dst;
+  for (size_t i = 0; i < P.fused_gates.size(); ++i)
+    if (g[i].cls == GC_BLOCK) g[i].gmask = base + P.fused_gates[i].gmask - i * sizeof(DevGate);
 }
 
 void plan_pass_pointers(const Plan &P, int idx, const void *d_blob, PassDesc &d) {
@@ -322,12 +337,17 @@ void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &o
       i += 4;
       continue;
     }
+    if (run[i].cls == GC_BLOCK) {  // dense blocks run on the tensor cores, between cubes
+      out.push_back(run[i]);
+      ++i;
+      continue;
+    }
     uint32_t bits = 0;
     int nb = 0;
     size_t j = i;
     for (; j < run.size(); ++j) {
       const DevGate &g = run[j];
-      if (g.cls == GC_DENSE4) break;
+      if (g.cls == GC_DENSE4 || g.cls == GC_BLOCK) break;
       if (!needs_pairing((int)g.cls) || g.target < 0) continue;
       const uint32_t tb = 1u << g.target;
       if (bits & tb) continue;
@@ -559,6 +579,20 @@ static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &pe
         }
       }
       ++ng;
+    }
+    d.nblocks = 0;
+    if (cfg.block_mode >= 0 && k >= 11 && ng > 1) {
+      const size_t first = P.pass_gate_offset.back();
+      std::vector<DevGate> run(P.fused_gates.begin() + first, P.fused_gates.end());
+      const int nb = group_blocks(run, k, cfg.block_mode, cfg.block_min_cost, P.block_data);
+      if (nb > 0) {
+        P.fused_gates.resize(first);
+        P.fused_gates.insert(P.fused_gates.end(), run.begin(), run.end());
+        d.nblocks = nb;
+        P.n_blocks += nb;
+        for (const DevGate &g : run)
+          if (g.cls == GC_BLOCK) P.n_block_gates += g.target;
+      }
     }
     if (cfg.cubes && k >= 8 && ng > 0) {
       const size_t first = P.pass_gate_offset.back();

@@ -19,6 +19,8 @@ struct PlanConfig {
   bool lookahead = true;    // grow a pass's chunk bits by simulated gate count (false: by immediate demand)
   bool merge = true;        // compose runs of one-qubit gates on one qubit into one matrix (FP64, host)
   uint64_t init_x = 0;
+  int block_mode = -1;      // >= 0: form dense tensor-core blocks (GC_BLOCK) for this arithmetic mode
+  double block_min_cost = 2.0;  // a block must replace at least this many dense one-qubit gate updates
 };
 
 struct Step {
@@ -34,6 +36,8 @@ struct Plan {
   std::vector<DevGate> fused_gates;
   std::vector<DevGate> sweep_gates;
   int n_fused_gates = 0, n_sweep_gates = 0, n_relabels = 0, n_skipped = 0, n_merged = 0;
+  int n_blocks = 0, n_block_gates = 0;
+  std::vector<unsigned char> block_data;  // operand planes of the GC_BLOCK records (see sv_internal.h)
   // Schedule record per source gate: the step that applies it (-1: folded into the layout or skipped) and
   // its position in execution order; per step the physical bits its chunks span (a sweep: its target bit).
   std::vector<int> gate_step, gate_order;
@@ -59,6 +63,12 @@ int validate_gate(const sv_gate &g, int n, std::string &why);
 // Split one pass's gates (chunk-local targets, in order) into register cubes: appends to `out` a GC_CUBE
 // header before each run.  Order is kept; every gate lands in exactly one cube.
 void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out);
+
+// Replace runs of a pass's gates (chunk-local targets, in order) by dense blocks on kBlockBits bits where that
+// saves at least `min_cost` dense one-qubit updates; appends each block's operand planes to `data` (header
+// gmask = their offset there).  Returns the number of blocks.
+int group_blocks(std::vector<DevGate> &run, int k, int mode, double min_cost, std::vector<unsigned char> &data);
+size_t block_data_bytes(int mode);
 
 // Validate a record sequence (two-qubit gates take four records); on error `bad` is the first bad record.
 int validate_records(const sv_gate *g, size_t ngates, int n, std::string &why, size_t &bad);

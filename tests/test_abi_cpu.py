@@ -255,3 +255,23 @@ def test_swaps_fold_into_layout(lib):
     n = 10
     plan = B.sv_plan_dry_run(n, B.SV_C128, C.pack(C.qft(n)))
     assert list(plan["final_perm"]) == list(range(n))[::-1]
+
+
+def _struct_fields(src, name):
+    body = re.search(r"typedef struct " + name + r" \{(.*?)\} " + name + ";", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        assert decl.startswith("uint64_t "), decl
+        fields += [f.strip() for f in decl[len("uint64_t "):].split(",")]
+    return fields
+
+
+def test_stats_structs_match_binding():
+    """The binding reads sv_batch_stats and sv_server_stats as arrays of uint64 in declaration order."""
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    assert _struct_fields(src, "sv_batch_stats") == B.BATCH_STATS_FIELDS
+    assert _struct_fields(src, "sv_server_stats") == B.SERVER_STATS_FIELDS
