@@ -99,6 +99,11 @@ typedef struct sv_server sv_server;
 #define SV_OPT_CUBES 8          /* complex64: 1 = apply runs of gates on at most 4 chunk bits from registers
                                    (one shared-memory round trip per run), the default; 0 = one
                                    shared-memory round trip per gate.  Results are identical either way. */
+#define SV_OPT_TENSOR_BLOCKS 10 /* complex64: 1 = compose runs of gates on at most 4 chunk bits into one 16 x 16
+                                   unitary (FP64, host; Sec. II.B's multi-qubit gate as a matrix) and apply it
+                                   with tcgen05 tensor-core MMAs in three bfloat16 splits (24 bits of each
+                                   factor, FP32 accumulation); 0 = per-gate arithmetic (the default).  Used for
+                                   fused passes with chunks of at least 2^11 amplitudes. */
 
 /* ---------------------------------------------------------------------------------------------------------
  * States
@@ -264,6 +269,10 @@ sv_status sv_sync(sv_state *s);
  * gates folded into the factors of a product state (sv_init_product).  Any pointer may be NULL. */
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
                              int *remaps, int *absorbed);
+
+/* Dense tensor-core blocks (SV_OPT_TENSOR_BLOCKS) of the last apply call: blocks applied and source gates they
+ * replaced.  Any pointer may be NULL. */
+sv_status sv_last_plan_blocks(sv_state *s, int *blocks, int *block_gates);
 
 /* With SV_OPT_PROFILE on: device time of the launches of the most recent apply call (or graph replay) of one
  * kind (0 = fused chunk pass, 1 = single-gate sweep), summed over its launches.  Waits for those launches.

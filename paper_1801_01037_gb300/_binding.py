@@ -41,6 +41,7 @@ SV_OPT_F64_SHARE = 7
 SV_OPT_CUBES = 8
 SV_F64_SHARE_DEFAULT = 16
 SV_OPT_PRODUCT_START = 9
+SV_OPT_TENSOR_BLOCKS = 10
 
 SV_GATE_U = 0
 SV_GATE_SWAP = 1
@@ -53,7 +54,7 @@ EXPORTED = [
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_run_batch_k", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version", "sv_last_batch_stats", "sv_server_pause",
-    "sv_server_get_stats",
+    "sv_server_get_stats", "sv_last_plan_blocks",
 ]
 
 BATCH_STATS_FIELDS = ["rounds", "mixed_rounds", "max_round_chunks", "total_chunks"]
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         "sv_last_batch_stats": [P],
         "sv_server_pause": [P, i],
         "sv_server_get_stats": [P, P],
+        "sv_last_plan_blocks": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -306,6 +308,12 @@ def sv_last_plan_stats(h: int) -> dict:
     v = [ctypes.c_int() for _ in range(6)]
     _check(load().sv_last_plan_stats(h, *[ctypes.byref(x) for x in v]))
     return dict(zip(["passes", "fused_gates", "sweep_gates", "relabels", "remaps", "absorbed"], [x.value for x in v]))
+
+
+def sv_last_plan_blocks(h: int) -> dict:
+    b, g = ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_last_plan_blocks(h, ctypes.byref(b), ctypes.byref(g)))
+    return {"blocks": b.value, "block_gates": g.value}
 
 
 def sv_profile_last(h: int, kind: int = 0):

@@ -66,7 +66,19 @@ PlanConfig plan_config(const sv_state *s) {
   if (s->chunk_k > 0) c.k = s->chunk_k;
   c.fusion = s->fusion != 0;
   c.cubes = s->dtype == SV_C64 && s->cubes != 0;
+  if (s->tensor_blocks && s->dtype == SV_C64) c.block_mode = MODE_C64_F32;
   return c;
+}
+
+int check_tc_error(sv_state *s) {
+  if (!s->tc_used || !s->d_sched) return SV_OK;
+  unsigned err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, &s->d_sched->tc_err, sizeof err, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core error word");
+  if (err == 0) return SV_OK;
+  cudaMemsetAsync(&s->d_sched->tc_err, 0, sizeof err, s->stream);
+  return set_error(SV_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs; the state is not valid");
 }
 
 int upload_plan(sv_state *s, const Plan &P, void **d_blob) {
@@ -177,6 +189,7 @@ int run_plan(sv_state *s, const Plan &P, const void *d_blob, cudaStream_t st, co
       for (int i = 0; moves_only && i < d.ngates; ++i)
         moves_only = P.fused_gates[P.pass_gate_offset[step.index] + i].cls == GC_X;
       e = launch_fused(d, moves_only ? (int)MODE_C128_F64 : mode, st, f64_share_of(s), s->d_sched);
+      if (d.nblocks > 0) s->tc_used = true;
     } else {
       e = launch_sweep(s->psi, s->n, mode, P.sweep_gates[step.index], st);
     }
@@ -469,6 +482,7 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
     case SV_OPT_CUBES: s->cubes = value ? 1 : 0; return SV_OK;
+    case SV_OPT_TENSOR_BLOCKS: s->tensor_blocks = value ? 1 : 0; return SV_OK;
     case SV_OPT_PRODUCT_START: s->product_start = value ? 1 : 0; return SV_OK;
     case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
     case SV_OPT_F64_SHARE:
@@ -540,6 +554,8 @@ static int apply_records(sv_state *s, const sv_gate *gates, size_t ngates, bool 
   s->st_fused = P.n_fused_gates;
   s->st_sweeps = P.n_sweep_gates;
   s->st_relabels = P.n_relabels;
+  s->st_blocks = P.n_blocks;
+  s->st_block_gates = P.n_block_gates;
   s->st_remaps = 0;
   if (s->canonical) return canonicalize_now(s);
   return SV_OK;
@@ -625,6 +641,13 @@ sv_status sv_plan_dry_run(int n, sv_dtype dtype, int chunk_k, const sv_gate *gat
   return SV_OK;
 }
 
+sv_status sv_last_plan_blocks(sv_state *s, int *blocks, int *block_gates) {
+  if (!s) return set_error(SV_ERR_ARG, "state is NULL");
+  if (blocks) *blocks = s->st_blocks;
+  if (block_gates) *block_gates = s->st_block_gates;
+  return SV_OK;
+}
+
 sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms) {
   if (!s || !launches || !ms) return set_error(SV_ERR_ARG, "NULL argument");
   *launches = 0;
@@ -645,7 +668,7 @@ sv_status sv_profile_last(sv_state *s, int kind, int *launches, double *ms) {
 sv_status sv_sync(sv_state *s) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
   cudaError_t e = cudaStreamSynchronize(s->stream);
-  return e == cudaSuccess ? SV_OK : cuda_fail(e, "stream sync");
+  return e == cudaSuccess ? check_tc_error(s) : cuda_fail(e, "stream sync");
 }
 
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels, int *remaps,

@@ -39,6 +39,7 @@ void plan_fresh(sv_state *s, const sv_gate *g, size_t ng, Plan &P) {
   cfg.init_x = 0;
   cfg.single_as_sweep = false;
   cfg.fusion = true;
+  cfg.block_mode = -1;  // the batched kernels apply gates one by one
   make_plan(s->n, cfg, s->perm, g, ng, P);
 }
 

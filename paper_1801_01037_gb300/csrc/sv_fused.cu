@@ -9,6 +9,7 @@
 // diagonal gate, wherever its target) is applied to the chunk in shared memory with the pair update of
 // Sec. V.A; control bits inside Q are inserted as fixed one-bits of the enumerated index (tested per
 // amplitude inside complex64 register cubes), control bits outside Q are tested once per chunk.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -307,6 +308,25 @@ constexpr int kTcRowBytes = kBlockK * 2;          // one row of one plane
 constexpr int kTcTileBytes = 128 * kTcRowBytes;   // 128 rows of one plane
 constexpr uint64_t kTcWaitNs = 2000000000ull;     // bound of one wait for the tensor cores
 
+// The planner keeps c >= min(3, k), so the row table never has more than max(1, 2^(k-3)) entries; 128 bytes
+// of permuted-store table follow it.
+template <int MODE>
+__host__ __device__ constexpr int smem_bytes(int k) {
+  return (int)(sizeof(typename Arith<MODE>::S) << k) + (int)(sizeof(uint64_t) << (k > 3 ? k - 3 : 0)) + 128;
+}
+
+// Tensor-core pass: the fused pass's shared memory, then (1024-byte aligned) the A planes of all rows, the B
+// planes of one block, the mbarrier and the TMEM address slot.
+template <int MODE>
+__host__ __device__ constexpr int tc_planes() { return MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128; }
+template <int MODE>
+__host__ __device__ constexpr int tc_smem_base(int k) { return (smem_bytes<MODE>(k) + 1023) & ~1023; }
+template <int MODE>
+__host__ __device__ constexpr int tc_smem_bytes(int k) {
+  return tc_smem_base<MODE>(k) + tc_planes<MODE>() * ((1 << (k - kBlockBits)) * kTcRowBytes) +
+         tc_planes<MODE>() * (int)kBlockPlaneBytes + 64;
+}
+
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                ::"r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
@@ -477,9 +497,9 @@ __device__ __forceinline__ void tc_block_c64(const DevGate &h, float2 *sm, int k
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
 // permuted store's table.
-template <int MODE, bool PACK = true>
+template <int MODE, bool PACK = true, bool TC = false>
 __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, typename Arith<MODE>::S *sm,
-                                            uint64_t *rowoff) {
+                                            uint64_t *rowoff, TcCtx *tc = nullptr) {
   using M = Arith<MODE>;
   using G = typename M::G;
   using S = typename M::S;
@@ -537,6 +557,10 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
 
   for (int gi = 0; gi < p.ngates; ++gi) {
     const DevGate &g = p.gates[gi];
+    if (g.cls == GC_BLOCK) {  // its gmask is the offset of its operand planes, not a control mask
+      if constexpr (TC && MODE == MODE_C64_F32) tc_block_c64(g, sm, k, *tc);
+      continue;
+    }
     const uint64_t gmask = g.gmask;
     if ((base & gmask) != gmask) continue;  // a control bit outside the chunk is 0: the gate skips this chunk
     const uint32_t cls = g.cls;
@@ -620,6 +644,45 @@ __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused(con
   S *sm = (S *)smraw;
   uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(S) << p.k));
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) fused_chunk<MODE>(p, ch, sm, rowoff);
+}
+
+// Fused pass whose gates include dense blocks (GC_BLOCK) for the tensor cores.  Warp 0 allocates `ncols` TMEM
+// columns for the CTA's accumulators (ncols * CTAs per SM <= 512, so the allocation never waits on a CTA of
+// this launch), thread 0 initialises the mbarrier the MMAs commit to; both are released at the end.
+template <int MODE>
+__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_tc(const PassDesc p, uint64_t nchunks, uint32_t ncols,
+                                                               unsigned *err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  using S = typename Arith<MODE>::S;
+  S *sm = (S *)smraw;
+  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(S) << p.k));
+  const uint32_t R = 1u << (p.k - kBlockBits);
+  TcCtx tc;
+  tc.opA = smraw + tc_smem_base<MODE>(p.k);
+  tc.opB = tc.opA + (size_t)tc_planes<MODE>() * R * kTcRowBytes;
+  tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)tc_planes<MODE>() * kBlockPlaneBytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tc.mbar + 1);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(tc.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc.tmem = *tslot;
+  tc.phase = 0;
+  tc.ok = 1;
+  tc.err = err;
+  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) fused_chunk<MODE, true, true>(p, ch, sm, rowoff, &tc);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(ncols) : "memory");
 }
 
 // Complex128 pass split between the SM's two arithmetic units.  The double-float path keeps the FP32 pipes
@@ -768,13 +831,6 @@ int sms() {
   return v;
 }
 
-// The planner keeps c >= min(3, k), so the row table never has more than max(1, 2^(k-3)) entries; 128 bytes
-// of permuted-store table follow it.
-template <int MODE>
-int smem_bytes(int k) {
-  return (int)(sizeof(typename Arith<MODE>::S) << k) + (int)(sizeof(uint64_t) << (k > 3 ? k - 3 : 0)) + 128;
-}
-
 template <int MODE>
 cudaError_t fused_launch(const PassDesc &p, cudaStream_t st) {
   const int smem = smem_bytes<MODE>(p.k);
@@ -822,8 +878,37 @@ int fused_smem_bytes(int mode, int k) {
   return mode == MODE_C64_F32 ? smem_bytes<MODE_C64_F32>(k) : smem_bytes<MODE_C128_F64>(k);
 }
 
+template <int MODE>
+cudaError_t tc_launch(const PassDesc &p, cudaStream_t st, FusedSched *sched) {
+  const int smem = tc_smem_bytes<MODE>(p.k);
+  static std::atomic<int> granted[64] = {};
+  cudaError_t e = ensure_smem((const void *)k_fused_tc<MODE>, smem, granted);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_tc<MODE>, kFusedThreads, smem);
+  if (occ < 1) occ = 1;
+  const uint32_t tiles = 1u << (p.k - kBlockBits - 7);
+  const uint32_t levels = MODE == MODE_C64_F32 ? 1u : 7u;
+  uint32_t ncols = 32;
+  while (ncols < tiles * levels * (uint32_t)kBlockK) ncols <<= 1;
+  if (ncols > 512) return cudaErrorInvalidValue;
+  occ = std::min<int>(occ, (int)(512 / ncols));
+  const uint64_t nchunks = 1ull << (p.n - p.k);
+  const uint64_t cap = (uint64_t)sms() * occ;
+  const unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
+  k_fused_tc<MODE><<<grid, kFusedThreads, smem, st>>>(p, nchunks, ncols, &sched->tc_err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_share, FusedSched *sched) {
   const uint64_t nchunks = 1ull << (p.n - p.k);
+  if (p.nblocks > 0) {
+    // dense blocks need the tensor-core kernel: chunks of at least 2^11 amplitudes (128-row tiles) and the
+    // scratch that carries its error word
+    if (sched == nullptr || p.k < kBlockBits + 7 || p.k > 13) return cudaErrorInvalidValue;
+    if (mode == MODE_C64_F32) return tc_launch<MODE_C64_F32>(p, st, sched);
+    return cudaErrorInvalidValue;
+  }
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {
     const int smem = smem_bytes<MODE_C128_DF32>(p.k);
     static std::atomic<int> granted[64] = {};

@@ -72,7 +72,7 @@ sv_status sv_read_amplitudes(sv_state *s, uint64_t first, uint64_t count, void *
   if (identity_layout(s)) {
     e = cudaMemcpyAsync(host_out, (const char *)s->psi + first * ab, count * ab, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return e == cudaSuccess ? SV_OK : cuda_fail(e, "read amplitudes");
+    return e == cudaSuccess ? check_tc_error(s) : cuda_fail(e, "read amplitudes");
   }
   const uint64_t chunk = std::min<uint64_t>(count, kReadChunk);
   if ((rc = ensure_read_buffer(s, chunk * ab)) != SV_OK) return rc;
@@ -84,7 +84,7 @@ sv_status sv_read_amplitudes(sv_state *s, uint64_t first, uint64_t count, void *
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gather amplitudes");
   }
-  return SV_OK;
+  return check_tc_error(s);
 }
 
 sv_status sv_read_amplitudes_at(sv_state *s, const uint64_t *idx, uint64_t count, void *host_out) {
@@ -161,7 +161,7 @@ sv_status sv_norm(sv_state *s, double *out) {
   cudaError_t e = launch_norm(s->psi, s->n, mode_of(s), s->d_scalars, d_out, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  return e == cudaSuccess ? SV_OK : cuda_fail(e, "norm");
+  return e == cudaSuccess ? check_tc_error(s) : cuda_fail(e, "norm");
 }
 
 sv_status sv_expect_z(sv_state *s, uint64_t mask, double *out) {
@@ -367,6 +367,8 @@ sv_status sv_apply_circuit_graph(sv_state *s, const sv_gate *gates, size_t ngate
   s->st_fused = P.n_fused_gates;
   s->st_sweeps = P.n_sweep_gates;
   s->st_relabels = P.n_relabels;
+  s->st_blocks = P.n_blocks;
+  s->st_block_gates = P.n_block_gates;
   auto ins = s->graphs.emplace(key, std::move(ent));
   s->last_evs = ins.first->second.evs.empty() ? nullptr : ins.first->second.evs.data();
   s->last_kind = ins.first->second.ev_kind;

@@ -34,6 +34,8 @@ struct sv_state {
   int chunk_k = 0;            // 0 = default
   int fusion = 1;
   int cubes = 1;              // complex64: register cubes in fused passes (SV_OPT_CUBES)
+  int tensor_blocks = 0;      // dense tensor-core blocks in fused passes (SV_OPT_TENSOR_BLOCKS)
+  bool tc_used = false;       // a tensor-core pass has run: read-backs check its error word
   int canonical = 0;
   int f64_share = -1;         // -1 = library default (SV_OPT_F64_SHARE)
   int64_t renorm_period = 0;
@@ -60,6 +62,7 @@ struct sv_state {
   size_t d_prod_cap = 0;      // bytes
   // stats of the last apply
   int st_passes = 0, st_fused = 0, st_sweeps = 0, st_relabels = 0, st_remaps = 0, st_absorbed = 0;
+  int st_blocks = 0, st_block_gates = 0;
   std::unordered_map<uint64_t, GraphEntry> graphs;
   // profiling (SV_OPT_PROFILE)
   int profile = 0;
@@ -98,6 +101,9 @@ int canonicalize_on(sv_state *s, std::vector<int> &perm, cudaStream_t st, int *n
 constexpr int kDefaultF64Share = SV_F64_SHARE_DEFAULT;
 int f64_share_of(const sv_state *s);
 int maybe_renormalize(sv_state *s, int applied);
+// After a synchronisation: SV_ERR_TIMEOUT if a tensor-core pass of the state reported a wait that ran out
+// (its error word is cleared); SV_OK otherwise.
+int check_tc_error(sv_state *s);
 int alloc_state(int n, sv_dtype dt, cudaStream_t st, sv_state **out, bool init_zero);
 
 } // namespace svi

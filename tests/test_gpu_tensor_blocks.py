@@ -1,0 +1,105 @@
+"""Dense gate blocks on the tensor cores (SV_OPT_TENSOR_BLOCKS): runs of gates on at most four chunk bits
+composed on the host into one 16 x 16 unitary (Sec. II.B: a multi-qubit gate acts as a matrix on its
+qubits' basis states) and applied to every row of the chunk with tcgen05 MMAs.  Every result is compared
+element by element with the FP64 oracle at the complex64 tolerance, and with the per-gate path, over
+several chunk sizes, circuit families (random layers, QFT with controlled phases, controlled and two-qubit
+gates) and ragged cases (chunks of one tile, states just above the chunk size)."""
+import numpy as np
+import pytest
+
+import circuits as C
+from gpu_helpers import assert_close, run_oracle
+
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_1801_01037_gb300")._binding
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1801_01037_gb300 import build
+    build.build()
+    B.load()
+
+
+def run(n, gates, dtype, blocks, chunk_k=0, x0=0, graph=False):
+    h = B.sv_create(n, dtype)
+    try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1 if blocks else 0)
+        if chunk_k:
+            B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k)
+        if x0:
+            B.sv_init_basis(h, x0)
+        (B.sv_apply_circuit_graph if graph else B.sv_apply_circuit)(h, gates)
+        st = B.sv_last_plan_blocks(h)
+        return B.sv_read_amplitudes(h).astype(np.complex128), st
+    finally:
+        B.sv_destroy(h)
+
+
+def mixed_circuit(n, rng, layers=3):
+    """Haar U(2) layers with CNOTs, controlled U(2) with 1-2 controls, diagonal phases and dense two-qubit
+    gates, on qubits spread over the whole register."""
+    g = []
+    for _ in range(layers):
+        for q in range(n):
+            g.append(C.gate_u(C.haar_u2(rng), q))
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            g.append(C.cnot(int(perm[i]), int(perm[i + 1])))
+        for _ in range(n // 2):
+            t, c1, c2 = (int(x) for x in rng.choice(n, 3, replace=False))
+            g.append(C.gate_u(C.haar_u2(rng), t, (c1,) if rng.random() < 0.5 else (c1, c2)))
+            g.append(C.gate_u(C.phase(rng.uniform(0, 2 * np.pi)), t, (c1,)))
+        for _ in range(max(1, n // 4)):
+            a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+            g.append(C.gate_u4(C.haar_u4(rng), a, b))
+    return C.pack(g)
+
+
+@pytest.mark.parametrize("n,chunk_k", [(11, 11), (12, 11), (12, 12), (13, 12), (14, 13), (17, 12), (20, 13)])
+def test_random_layers_on_tensor_cores_match_oracle(n, chunk_k):
+    w = C.random_workload(n, 4, seed=300 + n)
+    got, st = run(n, w.gates, B.SV_C64, True, chunk_k)
+    assert st["blocks"] > 0 and st["block_gates"] >= 2 * st["blocks"], st
+    want = run_oracle(n, w.gates)
+    assert_close(got, want, B.SV_C64, f"n={n} k={chunk_k} tensor blocks")
+    per_gate, st0 = run(n, w.gates, B.SV_C64, False, chunk_k)
+    assert st0["blocks"] == 0
+    assert_close(got, per_gate, B.SV_C64, "tensor blocks vs per-gate")
+
+
+@pytest.mark.parametrize("n,chunk_k", [(12, 12), (15, 11), (18, 13)])
+def test_mixed_gate_families_on_tensor_cores(n, chunk_k):
+    rng = np.random.Generator(np.random.PCG64(77 + n))
+    gates = mixed_circuit(n, rng)
+    got, st = run(n, gates, B.SV_C64, True, chunk_k)
+    assert st["blocks"] > 0, st
+    assert_close(got, run_oracle(n, gates), B.SV_C64, f"mixed n={n}")
+
+
+def test_qft_then_layers_on_tensor_cores():
+    w = C.qft_random_workload(16, 3, seed=5)
+    got, st = run(16, w.gates, B.SV_C64, True, 12, x0=w.x0)
+    assert st["blocks"] > 0, st
+    assert_close(got, run_oracle(16, w.gates, x0=w.x0), B.SV_C64, "qft + layers")
+
+
+def test_tensor_blocks_in_a_captured_graph_and_deep_circuit():
+    n = 22
+    w = C.random_workload(n, 12, seed=2024)
+    got, st = run(n, w.gates, B.SV_C64, True, 13, graph=True)
+    assert st["blocks"] > 0, st
+    want = run_oracle(n, w.gates)
+    assert_close(got, want, B.SV_C64, "graph, 12 layers, n=22")
+    again, _ = run(n, w.gates, B.SV_C64, True, 13, graph=False)
+    assert np.array_equal(got, again), "blocks are deterministic and the graph replays the same launches"
+
+
+def test_tensor_blocks_are_ignored_below_one_tile_and_for_complex128():
+    # chunks of fewer than 2^11 amplitudes (a 128-row tile) and complex128 states keep the per-gate path
+    w = C.random_workload(10, 3, seed=9)
+    got, st = run(10, w.gates, B.SV_C64, True)
+    assert st["blocks"] == 0
+    assert_close(got, run_oracle(10, w.gates), B.SV_C64, "n=10")
+    got, st = run(14, C.random_workload(14, 2, seed=9).gates, B.SV_C128, True)
+    assert st["blocks"] == 0
