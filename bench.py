@@ -307,7 +307,7 @@ def run_ours(args):
         return nrm, amps
 
     # Chunk size per dtype from the autotuner, timed on a 4-layer circuit of the same shape (untimed here).
-    chunk_k, tuning = {}, {}
+    chunk_k, tuning, tensor_blocks = {}, {}, {}
     f64_share = B.SV_F64_SHARE_DEFAULT  # share of chunks done on the FP64 pipe unless the autotuner picks one
     if not args.no_autotune:
         from paper_1801_01037_gb300 import autotune
@@ -315,6 +315,7 @@ def run_ours(args):
         for dt, ar in ((B.SV_C128, B.SV_ARITH_DF32), (B.SV_C64, B.SV_ARITH_AUTO)):
             res = autotune.tune(args.n, dt, probe, ar, save=False)
             chunk_k[dt] = res["best"]
+            tensor_blocks[dt] = int(res.get("best_tensor_blocks", 0))
             tuning["c128" if dt == B.SV_C128 else "c64"] = res
             if dt == B.SV_C128:
                 f64_share = int(res["best_f64_share"])
@@ -328,6 +329,8 @@ def run_ours(args):
                 B.sv_set_option(h, B.SV_OPT_F64_SHARE, f64_share)
             if dtype in chunk_k:
                 B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k[dtype])
+            if arith != B.SV_ARITH_F64:
+                B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, tensor_blocks.get(dtype, 0))
             B.sv_set_option(h, B.SV_OPT_PROFILE, 1 if profile else 0)
             graph = renorm == 0  # renormalisation runs between launches, so not inside a captured graph
             for _ in range(warmup):
@@ -352,6 +355,7 @@ def run_ours(args):
             barrier(dist)
             ms = e0.elapsed_time(e1)
             stats = B.sv_last_plan_stats(h)
+            stats.update(B.sv_last_plan_blocks(h))
             return {"ms": ms, "norm": nrm, "fused_launches": fused_launches, "fused_ms": fused_ms, "stats": stats,
                     "clocks": clocks}
         finally:
@@ -395,6 +399,7 @@ def run_ours(args):
         if B.SV_C128 in chunk_k:
             B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k[B.SV_C128])
         B.sv_set_option(h, B.SV_OPT_F64_SHARE, f64_share)
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, tensor_blocks.get(B.SV_C128, 0))
         for _ in range(max(1, args.warmup)):
             step(h, graph=False)
         torch.cuda.synchronize()
@@ -506,12 +511,15 @@ def run_ours(args):
         "batched": batched,
         "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
                  "fused_gates_per_step": c128["stats"]["fused_gates"],
-                 "folded_into_product_start": c128["stats"]["absorbed"]},
+                 "folded_into_product_start": c128["stats"]["absorbed"],
+                 "tensor_blocks_per_step": c128["stats"]["blocks"], "gates_in_tensor_blocks": c128["stats"]["block_gates"],
+                 "tensor_blocks_option": {"c128": tensor_blocks.get(B.SV_C128, 0), "c64": tensor_blocks.get(B.SV_C64, 0)}},
         # The method's roofline of the dominant kernel (algorithmic bytes: one read and one write of the state
         # per fused pass, against the measured HBM copy bandwidth).  The pass is limited by arithmetic issue, not
         # by HBM: its FP32-pipe and FP64-pipe views follow, and its FP64-equivalent flop rate.
-        "roofline": {"kernel": ("k_fused_mixed (c128 fused chunk pass: double-float CTAs + one FP64 CTA per SM)"
-                                if f64_share > 0 else "k_fused<c128, double-float> (fused chunk pass)"),
+        "roofline": {"kernel": (("k_fused_tc (passes with dense tcgen05 blocks) and " if c128["stats"]["blocks"] else "")
+                                + ("k_fused_mixed (c128 fused chunk pass: double-float CTAs + one FP64 CTA per SM)"
+                                   if f64_share > 0 else "k_fused<c128, double-float> (fused chunk pass)")),
                      "bound": "hbm", "achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
                      "frac": (hbm_achieved / peak) if hbm_achieved else None, "traffic": traffic,
                      "algorithmic_bytes_per_launch": 2 * state_bytes, "avg_launch_ms": avg_ms,
@@ -526,6 +534,7 @@ def run_ours(args):
                                   "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
                                   "note": "operations of the double-float method itself (its chosen arithmetic)"},
                      "f64_share_percent": f64_share,
+                     "tensor_core_view": tensor_view(c128, args.n, chunk_k.get(B.SV_C128, 12), avg_ms, sm_hz),
                      "fp64_pipe_view": {"achieved": f64_achieved, "peak": f64_peak, "unit": "T FP64 FMA/s",
                                         "frac": (f64_achieved / f64_peak) if f64_achieved else None,
                                         "peak_source": "152 SMs x 1.73 FP64 FMA/clock (probe) x median SM clock"}},
@@ -543,6 +552,28 @@ def run_ours(args):
         "norm_last_step": c128["norm"],
     }
     print(json.dumps(line), flush=True)
+
+
+def tensor_view(run, n, k, avg_ms, sm_hz):
+    """bf16 tensor-core work of the dense complex128 blocks: per block and chunk of 2^k amplitudes, 2^(k-11) tiles
+    of 128 rows x 26 digit products x 2 MMAs of 128 x 32 x 16 multiply-adds.  Averaged over the fused launches of
+    the step (blocks run in some of them), against the measured bf16 dense peak scaled to the sampled clock."""
+    blocks = run["stats"].get("blocks", 0)
+    if not blocks or not run["fused_launches"]:
+        return None
+    flops_step = blocks * 2.0 ** (n - k) * 2 ** (k - 11) * 26 * 2 * (128 * 32 * 16) * 2
+    flops_launch = flops_step / max(1, run["stats"]["passes"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        peak = float(pk["bf16_tflops_sustained"]) * (sm_hz / float(pk.get("sm_max_mhz", 2070.0)))
+        src = "measured bf16_tflops_sustained x sampled / max SM clock"
+    except Exception:
+        peak, src = 1700.0, "fallback sustained bf16 (1.7 PFLOP/s)"
+    ach = flops_launch / (avg_ms * 1e-3) / 1e12
+    return {"achieved": ach, "peak": peak, "unit": "TFLOP/s (bf16 MMA)", "frac": ach / peak,
+            "flops_per_launch": flops_launch, "blocks_per_step": blocks, "peak_source": src,
+            "note": "exact base-256 digit products: 26 bf16 MMA products per block row tile"}
 
 
 # FP32-pipe operations of the double-float method per amplitude (integer, float add/sub, FMA and conversion

@@ -3,7 +3,8 @@
 The fused pass holds 2^k amplitudes per CTA in shared memory.  A larger k lets a pass take more gates (fewer
 passes, fewer HBM sweeps) but leaves fewer CTAs per SM to hide each other's load and barrier latency.  This
 module times candidate k on the GPU through the C ABI (``SV_OPT_CHUNK_QUBITS``) for a circuit of the caller's
-shape, then (complex128, double-float) the share of chunks given to the FP64 pipe (``SV_OPT_F64_SHARE``),
+shape, then (complex128, double-float) the share of chunks given to the FP64 pipe (``SV_OPT_F64_SHARE``) and
+whether dense tensor-core blocks pay (``SV_OPT_TENSOR_BLOCKS``),
 keeps the fastest per (n, dtype, arithmetic) in a JSON cache, and applies it to a state.
 
 Cache file: ``$SV_AUTOTUNE_CACHE`` or ``~/.cache/gb300_statevec_autotune.json``.
@@ -46,17 +47,21 @@ def save_cache(cache: dict) -> None:
 
 
 F64_SHARES = (0, 10, 12, 14, 16, 18, 20)
+TENSOR_BLOCKS = (0, 4)
 
 
-def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1) -> float:
+def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1,
+                   tensor_blocks: int = 0) -> float:
     """Best device time (ms, summed over the fused-pass launches) of one application of `gates` with 2^k chunks
-    (and, for complex128, `f64_share` percent of the chunks in native FP64)."""
+    (and, for complex128, `f64_share` percent of the chunks in native FP64; `tensor_blocks` as the option
+    SV_OPT_TENSOR_BLOCKS)."""
     h = B.sv_create(n, dtype)
     try:
         if dtype == B.SV_C128:
             B.sv_set_option(h, B.SV_OPT_ARITH, arith)
             B.sv_set_option(h, B.SV_OPT_F64_SHARE, f64_share)
         B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, k)
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, tensor_blocks)
         B.sv_set_option(h, B.SV_OPT_PROFILE, 1)
         best = float("inf")
         for _ in range(repeats + 1):  # the first run captures the graph
@@ -84,10 +89,17 @@ def tune(n: int, dtype: int, gates, arith: int = B.SV_ARITH_AUTO, candidates=Non
     ms = {k: time_candidate(n, dtype, arith, gates, k) for k in cands}
     best = min(ms, key=ms.get)
     res = {"best": best, "ms": {str(k): v for k, v in ms.items()}}
+    share = -1
     if dtype == B.SV_C128 and arith != B.SV_ARITH_F64:
         sh = {s: time_candidate(n, dtype, arith, gates, best, f64_share=s) for s in F64_SHARES}
-        res["best_f64_share"] = min(sh, key=sh.get)
+        share = min(sh, key=sh.get)
+        res["best_f64_share"] = share
         res["f64_share_ms"] = {str(s): v for s, v in sh.items()}
+    if arith != B.SV_ARITH_F64:
+        # dense tensor-core blocks (off, or blocks that replace at least 4 dense one-qubit updates)
+        tb = {t: time_candidate(n, dtype, arith, gates, best, f64_share=share, tensor_blocks=t) for t in TENSOR_BLOCKS}
+        res["best_tensor_blocks"] = min(tb, key=tb.get)
+        res["tensor_blocks_ms"] = {str(t): v for t, v in tb.items()}
     if save:
         cache = load_cache()
         cache[_key(n, dtype, arith)] = res
@@ -110,4 +122,6 @@ def apply(h: int, arith: int = B.SV_ARITH_AUTO) -> int | None:
     B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, int(ent["best"]))
     if "best_f64_share" in ent:
         B.sv_set_option(h, B.SV_OPT_F64_SHARE, int(ent["best_f64_share"]))
+    if "best_tensor_blocks" in ent:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, int(ent["best_tensor_blocks"]))
     return int(ent["best"])

@@ -66,7 +66,11 @@ PlanConfig plan_config(const sv_state *s) {
   if (s->chunk_k > 0) c.k = s->chunk_k;
   c.fusion = s->fusion != 0;
   c.cubes = s->dtype == SV_C64 && s->cubes != 0;
+  // Dense tensor-core blocks: complex64, and complex128 in double-float arithmetic with chunks of at most 2^12
+  // amplitudes (the digit planes of larger chunks do not fit in shared memory).
   if (s->tensor_blocks && s->dtype == SV_C64) c.block_mode = MODE_C64_F32;
+  if (s->tensor_blocks && mode_of(s) == MODE_C128_DF32 && c.k <= 12) c.block_mode = MODE_C128_DF32;
+  if (s->tensor_blocks >= 2) c.block_min_cost = (double)s->tensor_blocks;
   return c;
 }
 
@@ -482,7 +486,10 @@ sv_status sv_set_option(sv_state *s, int option, int64_t value) {
       return SV_OK;
     case SV_OPT_FUSION: s->fusion = value ? 1 : 0; return SV_OK;
     case SV_OPT_CUBES: s->cubes = value ? 1 : 0; return SV_OK;
-    case SV_OPT_TENSOR_BLOCKS: s->tensor_blocks = value ? 1 : 0; return SV_OK;
+    case SV_OPT_TENSOR_BLOCKS:
+      if (value < 0 || value > 64) return set_error(SV_ERR_ARG, "tensor blocks: 0 (off), 1 (on) or 2..64 (minimum size)");
+      s->tensor_blocks = (int)value;
+      return SV_OK;
     case SV_OPT_PRODUCT_START: s->product_start = value ? 1 : 0; return SV_OK;
     case SV_OPT_PROFILE: s->profile = value ? 1 : 0; return SV_OK;
     case SV_OPT_F64_SHARE:

@@ -150,8 +150,11 @@ void encode_planes(int mode, const double (*W)[kBlockK], unsigned char *dst) {
       } else {
         int64_t v = (int64_t)std::llround(std::ldexp(W[n][kk], 47));
         for (int s = 0; s < kBlockDigitsC128; ++s) {
-          int64_t d = ((v % 256) + 256) % 256;  // v mod 256 in [0, 256)
-          if (d >= 128) d -= 256;               // balanced digit in [-128, 128)
+          int64_t d = v;                          // the top digit keeps what is left: |v| <= 2^47 gives [-128, 128]
+          if (s + 1 < kBlockDigitsC128) {
+            d = ((v % 256) + 256) % 256;          // v mod 256 in [0, 256)
+            if (d >= 128) d -= 256;               // balanced digit in [-128, 128)
+          }
           p[s] = bf16_bits((double)d);
           v = (v - d) / 256;
         }

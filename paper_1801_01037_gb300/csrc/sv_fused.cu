@@ -76,18 +76,18 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // All pairs (j0, j0 | tb) of the chunk for one gate of class CLS, target bit t, local controls cm.
 // PACK: dense double-float pairs in packed FP32x2 instructions (Arith::pair) or in scalar ones
 // (Arith::pair_scalar, for the batched kernels, whose extra live state made the packed form spill).
-template <int MODE, int CLS, bool PACK = true>
+template <int MODE, int CLS, bool PACK = true, int NT = kFusedThreads>
 __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const typename Arith<MODE>::Coef &cf,
                                             uint32_t half, int t, uint32_t tb, uint32_t cm) {
   using S = typename Arith<MODE>::S;
   if constexpr (MODE == MODE_C128_DF32 && CLS == GC_GENERAL && PACK) {
-    if (cm == 0 && (half % (2 * kFusedThreads)) == 0) {
+    if (cm == 0 && (half % (2 * NT)) == 0) {
       // Double-float dense gates, no local control: two pairs per thread loaded before either is computed,
       // so their dependency chains interleave (the compiler cannot move a load above the previous pair's
-      // stores to shared memory by itself).  Pairs i and i + kFusedThreads are disjoint.
+      // stores to shared memory by itself).  Pairs i and i + NT are disjoint.
 #pragma unroll 1
-      for (uint32_t i = threadIdx.x; i < half; i += 2 * kFusedThreads) {
-        const uint32_t j0 = ins0(i, t), j1 = ins0(i + kFusedThreads, t);
+      for (uint32_t i = threadIdx.x; i < half; i += 2 * NT) {
+        const uint32_t j0 = ins0(i, t), j1 = ins0(i + NT, t);
         const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
         const uint32_t s2 = slot<MODE>(j1), s3 = slot<MODE>(j1 | tb);
         S a = sm[s0], b = sm[s1], a1 = sm[s2], b1 = sm[s3];
@@ -105,7 +105,7 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
     // Local controls: only the half >> popc(cm) pairs whose control bits are all 1, enumerated directly.
     const uint32_t cnt = half >> __popc(cm);
 #pragma unroll pair_unroll<MODE>()
-    for (uint32_t i = threadIdx.x; i < cnt; i += kFusedThreads) {
+    for (uint32_t i = threadIdx.x; i < cnt; i += NT) {
       const uint32_t j0 = expand_fixed(i, tb | cm, cm);
       const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
       S a = sm[s0], b = sm[s1];
@@ -116,7 +116,7 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
     return;
   }
 #pragma unroll pair_unroll<MODE>()
-  for (uint32_t i = threadIdx.x; i < half; i += kFusedThreads) {
+  for (uint32_t i = threadIdx.x; i < half; i += NT) {
     const uint32_t j0 = ins0(i, t);
     if ((j0 & cm) != cm) continue;
     const uint32_t s0 = slot<MODE>(j0), s1 = slot<MODE>(j0 | tb);
@@ -130,14 +130,14 @@ __device__ __forceinline__ void chunk_pairs(typename Arith<MODE>::S *sm, const t
 // All quadruples of the chunk for a dense two-qubit gate (GC_DENSE4 + three GC_ROW records): chunk bits t0
 // (index bit b0 of the gate's matrix) and t1 (b1), local controls cm.  The four outputs are computed from
 // the old values before any is stored.
-template <int MODE>
+template <int MODE, int NT = kFusedThreads>
 __device__ __noinline__ void chunk_quads(typename Arith<MODE>::S *sm, const DevGate *rows, uint32_t nquads, int t0,
                                             int t1, uint32_t cm) {
   using M = Arith<MODE>;
   using S = typename M::S;
   const int lo = t0 < t1 ? t0 : t1, hi = t0 < t1 ? t1 : t0;
   const uint32_t b0 = 1u << t0, b1 = 1u << t1;
-  for (uint32_t i = threadIdx.x; i < nquads; i += kFusedThreads) {
+  for (uint32_t i = threadIdx.x; i < nquads; i += NT) {
     const uint32_t j = ins0(ins0(i, lo), hi);
     if ((j & cm) != cm) continue;
     const uint32_t s0 = slot<MODE>(j), s1 = slot<MODE>(j | b0), s2 = slot<MODE>(j | b1), s3 = slot<MODE>(j | b0 | b1);
@@ -223,7 +223,7 @@ __device__ __forceinline__ uint32_t cube_xoff(int s, const uint32_t (&soff)[CB])
 
 // The cube's `cnt` gates over the CB chunk bits packed in `posw` (one byte each, ascending), for every base
 // index of the chunk.
-template <int CB>
+template <int CB, int NT = kFusedThreads>
 __device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint64_t posw, uint64_t base, float2 *sm, int k) {
   int p[CB];
   uint32_t soff[CB], cube = 0;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void cube_run(const DevGate *gs, int cnt, uint64_t po
     soff[j] = slot<MODE_C64_F32>(1u << p[j]);
   }
   const uint32_t nbase = 1u << (k - CB);
-  for (uint32_t bi = threadIdx.x; bi < nbase; bi += kFusedThreads) {
+  for (uint32_t bi = threadIdx.x; bi < nbase; bi += NT) {
     uint32_t bidx = bi;
 #pragma unroll
     for (int j = 0; j < CB; ++j) bidx = ins0(bidx, p[j]);
@@ -324,7 +324,7 @@ __host__ __device__ constexpr int tc_smem_base(int k) { return (smem_bytes<MODE>
 template <int MODE>
 __host__ __device__ constexpr int tc_smem_bytes(int k) {
   return tc_smem_base<MODE>(k) + tc_planes<MODE>() * ((1 << (k - kBlockBits)) * kTcRowBytes) +
-         tc_planes<MODE>() * (int)kBlockPlaneBytes + 64;
+         2 * tc_planes<MODE>() * (int)kBlockPlaneBytes + 256;
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -348,40 +348,46 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t ph) {
   }
 }
 
-// 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tc_load32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
+// Work split of the tensor-core pass (kTcThreads threads): warp groups 2p and 2p + 1 form pair p, which takes
+// tiles p, p + kTcPairs, ..; in each tile, warp group 2p + h builds and reads back part h of every row
+// (h = 0: the real parts, K columns 0..15 and outputs 0..15; h = 1: the imaginary parts, 16..31), so every
+// warp group has work even for a chunk of two tiles.  TMEM lanes 32 (w % 4) .. + 31 belong to warp w, so each
+// warp group reads all 128 lanes (rows) of a tile.
+constexpr int kTcThreads = 512;
+constexpr int kTcGroups = kTcThreads / 128;
+constexpr int kTcPairs = kTcGroups / 2;
+constexpr int kTcMaxTiles = 4;                    // 2^13-amplitude chunks: 512 rows
 
 // Per-CTA state of the tensor-core pass (the same in every thread).
 struct TcCtx {
   unsigned char *opA;   // A planes: plane-major, rows x kTcRowBytes each
-  unsigned char *opB;   // B planes: kBlockPlaneBytes each
-  uint64_t *mbar;
+  unsigned char *opB;   // B planes, one set per pair (kTcPairs x planes x kBlockPlaneBytes)
+  uint64_t *mbar;       // one mbarrier per tile
   uint32_t tmem;        // TMEM address of this CTA's accumulators (lane 0, first column)
-  uint32_t phase;       // parity of the next mbarrier phase
+  uint32_t phase;       // parity of the next phase of every tile's mbarrier
   int ok;               // 0 once a wait ran out: later blocks are skipped
   unsigned *err;        // global error word
+  float *red;           // kTcThreads / 32 floats of shared scratch (complex128 chunk norm)
+  float sc, isc;        // complex128: 2^(47 - E) and 2^(E - 62) for the current chunk's exponent E
 };
 
-// Row r's base slot and the 16 slot offsets of its amplitudes (slot maps are linear over GF(2)).
+// Row r's base slot (its index with zeros at the block bits, through the slot map).
 template <int MODE>
-__device__ __forceinline__ void tc_row_slots(uint32_t r, const int (&pb)[kBlockBits], uint32_t &b0) {
+__device__ __forceinline__ uint32_t tc_row_base(uint32_t r, const int (&pb)[kBlockBits]) {
   uint32_t bidx = r;
 #pragma unroll
   for (int j = 0; j < kBlockBits; ++j) bidx = ins0(bidx, pb[j]);
-  b0 = slot<MODE>(bidx);
+  return slot<MODE>(bidx);
+}
+
+// Slot offset of element s of a row: the block bits set in s, through the slot map (linear over GF(2)).
+template <int MODE>
+__device__ __forceinline__ uint32_t tc_elem(int s, const int (&pb)[kBlockBits]) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int j = 0; j < kBlockBits; ++j)
+    if (s & (1 << j)) x ^= slot<MODE>(1u << pb[j]);
+  return x;
 }
 
 // 16-byte store of eight bfloat16 values (four packed pairs).
@@ -389,115 +395,305 @@ __device__ __forceinline__ void st_planes(unsigned char *dst, uint32_t w0, uint3
   *reinterpret_cast<uint4 *>(dst) = make_uint4(w0, w1, w2, w3);
 }
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+__device__ __forceinline__ uint32_t bf2_pack(float a, float b) { return bf2_bits(__floats2bfloat162_rn(a, b)); }
 
-// Complex64 block: rows split into three bfloat16 planes (x = x0 + x1 + x2, 24 bits), six products.
-__device__ __forceinline__ void tc_block_c64(const DevGate &h, float2 *sm, int k, TcCtx &tc) {
-  const uint32_t tid = threadIdx.x;
-  const uint32_t R = 1u << (k - kBlockBits);
-  const unsigned char *planes = reinterpret_cast<const unsigned char *>(&h) + h.gmask;
-  // B planes (the block's matrix) into shared memory.
-  for (uint32_t u = tid; u < (uint32_t)(kBlockSplitsC64 * kBlockPlaneBytes / 16); u += kFusedThreads)
-    cp_async16(tc.opB + 16u * u, planes + 16u * u);
-  int pb[kBlockBits];
-  uint32_t xo[kBlockDim];
+__device__ __forceinline__ void pair_sync(uint32_t pair) {
+  asm volatile("bar.sync %0, 256;" ::"r"(pair + 1u) : "memory");
+}
+
+// Issue tile t's MMAs for the (A plane, B plane, accumulator column) products of `Prod` and commit them to
+// the tile's mbarrier.  Called by one thread.
+template <int MODE>
+__device__ __forceinline__ void tc_issue(const TcCtx &tc, uint32_t t, uint32_t R, const unsigned char *myB) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t a0 = smem_addr(tc.opA) + t * kTcTileBytes, bb0 = smem_addr(myB);
+  if constexpr (MODE == MODE_C64_F32) {
+    const uint32_t d = tc.tmem + t * kBlockK;
+    uint32_t acc = 0;
+    // products x_i w_j with i + j <= 2 (i: A plane, j: B plane), one accumulator
 #pragma unroll
-  for (int j = 0; j < kBlockBits; ++j) pb[j] = (int)((h.cmask >> (8 * j)) & 0xffu);
+    for (int pr = 0; pr < 6; ++pr) {
+      const int i = pr == 2 || pr == 4 ? 1 : pr == 5 ? 2 : 0;
+      const int j = pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0;
 #pragma unroll
-  for (int s = 0; s < kBlockDim; ++s) {
-    uint32_t x = 0;
-#pragma unroll
-    for (int j = 0; j < kBlockBits; ++j)
-      if (s & (1 << j)) x ^= slot<MODE_C64_F32>(1u << pb[j]);
-    xo[s] = x;
-  }
-  // A planes: row r at (r / 8) * 512 + (r % 8) * 16 in each 128-row tile; K groups of 8 columns 128 bytes apart.
-  for (uint32_t r = tid; r < R; r += kFusedThreads) {
-    uint32_t b0;
-    tc_row_slots<MODE_C64_F32>(r, pb, b0);
-    float re[kBlockDim], im[kBlockDim];
-#pragma unroll
-    for (int s = 0; s < kBlockDim; ++s) {
-      const float2 v = sm[b0 ^ xo[s]];
-      re[s] = v.x;
-      im[s] = v.y;
-    }
-    unsigned char *row = tc.opA + (r / 8) * 512 + (r % 8) * 16;
-#pragma unroll
-    for (int pl = 0; pl < kBlockSplitsC64; ++pl) {
-      uint32_t w[16];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        // pairs (2q, 2q + 1): Re for q < 8 ... written as K columns 0..15 (Re) and 16..31 (Im)
-        const __nv_bfloat162 hr = __floats2bfloat162_rn(re[2 * q], re[2 * q + 1]);
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(im[2 * q], im[2 * q + 1]);
-        w[q] = bf2_bits(hr);
-        w[8 + q] = bf2_bits(hi);
-        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
-        re[2 * q] -= fr.x;
-        re[2 * q + 1] -= fr.y;
-        im[2 * q] -= fi.x;
-        im[2 * q + 1] -= fi.y;
+      for (int ks = 0; ks < kBlockK / 16; ++ks) {
+        tc_mma(d, tc_desc(a0 + (uint32_t)i * R * kTcRowBytes + (uint32_t)ks * 256),
+               tc_desc(bb0 + (uint32_t)j * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), acc);
+        acc = 1;
       }
-      unsigned char *dst = row + (size_t)pl * R * kTcRowBytes;
-      st_planes(dst + 0 * 128, w[0], w[1], w[2], w[3]);
-      st_planes(dst + 1 * 128, w[4], w[5], w[6], w[7]);
-      st_planes(dst + 2 * 128, w[8], w[9], w[10], w[11]);
-      st_planes(dst + 3 * 128, w[12], w[13], w[14], w[15]);
     }
-  }
-  cp_async_wait_all();
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
-  const uint32_t ntiles = R / 128;
-  if (tid == 0 && tc.ok) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t a0 = smem_addr(tc.opA), b0 = smem_addr(tc.opB);
-    for (uint32_t t = 0; t < ntiles; ++t) {
-      const uint32_t d = tc.tmem + t * kBlockK;
+  } else {
+    // digit products t_a u_b with a + b = L accumulated per level L = 4..10
+#pragma unroll 1
+    for (int L = 4; L <= 10; ++L) {
+      const uint32_t d = tc.tmem + t * (7 * kBlockK) + (uint32_t)(L - 4) * kBlockK;
       uint32_t acc = 0;
-      // products x_i w_j with i + j <= 2 (i: A plane, j: B plane)
-#pragma unroll
-      for (int pr = 0; pr < 6; ++pr) {
-        const int i = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
-        const int j = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+      const int alo = L > 5 ? L - 5 : 0, ahi = L < 5 ? L : 5;
+#pragma unroll 1
+      for (int a = alo; a <= ahi; ++a) {
 #pragma unroll
         for (int ks = 0; ks < kBlockK / 16; ++ks) {
-          const uint32_t aa = a0 + (uint32_t)i * R * kTcRowBytes + t * kTcTileBytes + (uint32_t)ks * 256;
-          const uint32_t bb = b0 + (uint32_t)j * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256;
-          tc_mma(d, tc_desc(aa), tc_desc(bb), acc);
+          tc_mma(d, tc_desc(a0 + (uint32_t)a * R * kTcRowBytes + (uint32_t)ks * 256),
+                 tc_desc(bb0 + (uint32_t)(L - a) * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), acc);
           acc = 1;
         }
       }
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(tc.mbar))
-                 : "memory");
   }
-  // Every thread waits for the MMAs (bounded); a wait that ran out stops the tensor-core work of this CTA.
-  int ok = tc.ok ? (tc_wait(tc.mbar, tc.phase) ? 1 : 0) : 0;
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(tc.mbar + t))
+               : "memory");
+}
+
+// ---- complex64 parts ----
+// A planes of part h of row r: the 16 components split into three bfloat16 planes x = x0 + x1 + x2.
+__device__ __forceinline__ void tc_rows_c64(const float2 *sm, uint32_t b0, const int (&pb)[kBlockBits], uint32_t h,
+                                            unsigned char *row, uint32_t R) {
+  float x[kBlockDim];
+#pragma unroll
+  for (int s = 0; s < kBlockDim; ++s) {
+    const float2 v = sm[b0 ^ tc_elem<MODE_C64_F32>(s, pb)];
+    x[s] = h ? v.y : v.x;
+  }
+#pragma unroll
+  for (int pl = 0; pl < kBlockSplitsC64; ++pl) {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+      w[q] = bf2_bits(b);
+      if (pl + 1 < kBlockSplitsC64) {
+        const float2 f = __bfloat1622float2(b);
+        x[2 * q] -= f.x;
+        x[2 * q + 1] -= f.y;
+      }
+    }
+    unsigned char *dst = row + (size_t)pl * R * kTcRowBytes + h * 256;
+    st_planes(dst, w[0], w[1], w[2], w[3]);
+    st_planes(dst + 128, w[4], w[5], w[6], w[7]);
+  }
+}
+
+// Outputs 16 h .. 16 h + 15 of this lane's row (16 TMEM columns), load and wait in one asm statement.
+__device__ __forceinline__ void tc_load16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- complex128 parts: exact digit products ----
+// x (a double-float h + l with |x| < 2^E, E fixed per chunk: the chunk's 2-norm, which its unitary gates
+// preserve, bounds every amplitude) is scaled to v = x 2^(47 - E), |v| <= 2^47, and written as six balanced
+// base-256 digits t_a in [-128, 128] (v ~ sum_a t_a 256^a), each exact in bfloat16.  With the matrix's digits
+// u_b of w 2^47 (host), every product t_a u_b is an exact integer below 2^14; the products of one digit level
+// L = a + b, summed over K = 32 terms and at most 6 pairs, stay below 2^22, so the FP32 accumulation in TMEM
+// is exact.  Levels 4..10 are kept (26 products): the dropped levels are below 2^-45 of |x|'s bound.
+__device__ __forceinline__ float rint_small(float x) {  // round to nearest integer, |x| < 2^22
+  return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
+}
+
+// Six balanced base-256 digits of v = (h + l) * sc (see above); t[0] least significant.
+__device__ __forceinline__ void df_digits(float h, float l, float sc, float (&t)[6]) {
+  float H = __fmul_rn(h, sc), L = __fmul_rn(l, sc);
+  t[5] = rint_small(__fmul_rn(H, 0x1p-40f));
+  H = __fmaf_rn(-t[5], 0x1p40f, H);
+  t[4] = rint_small(__fmul_rn(H, 0x1p-32f));
+  H = __fmaf_rn(-t[4], 0x1p32f, H);
+  float e;
+  two_sum(H, L, H, e);
+  L = e;
+  t[3] = rint_small(__fmul_rn(H, 0x1p-24f));
+  H = __fmaf_rn(-t[3], 0x1p24f, H);
+  t[2] = rint_small(__fmul_rn(H, 0x1p-16f));
+  H = __fmaf_rn(-t[2], 0x1p16f, H);
+  two_sum(H, L, H, e);
+  L = e;
+  t[1] = rint_small(__fmul_rn(H, 0x1p-8f));
+  H = __fmaf_rn(-t[1], 0x1p8f, H);
+  t[0] = rint_small(__fadd_rn(H, L));
+}
+
+// A planes of part h of row r: six digit planes of the 16 components (groups of 8 columns).
+__device__ __forceinline__ void tc_rows_c128(const float4 *sm, uint32_t b0, const int (&pb)[kBlockBits], uint32_t h,
+                                             unsigned char *row, uint32_t R, float sc) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float dg[8][6];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float4 v = sm[b0 ^ tc_elem<MODE_C128_DF32>(q * 8 + e, pb)];
+      if (h) df_digits(v.z, v.w, sc, dg[e]);
+      else df_digits(v.x, v.y, sc, dg[e]);
+    }
+#pragma unroll
+    for (int a = 0; a < kBlockDigitsC128; ++a)
+      st_planes(row + (size_t)a * R * kTcRowBytes + h * 256 + q * 128, bf2_pack(dg[0][a], dg[1][a]),
+                bf2_pack(dg[2][a], dg[3][a]), bf2_pack(dg[4][a], dg[5][a]), bf2_pack(dg[6][a], dg[7][a]));
+  }
+}
+
+// Columns 4 g .. 4 g + 3 of part h of every digit level of one tile, for this lane (28 values), in one asm
+// statement ending with the load wait.  a = TMEM address of level 0's first column of the part, + 4 g.
+__device__ __forceinline__ void tc_load_levels(uint32_t a, float (&d)[7][4]) {
+  uint32_t r[28];
+  asm volatile(
+      "{\n"
+      ".reg .b32 ta;\n"
+      "add.u32 ta, %28, 0;\n"   "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [ta];\n"
+      "add.u32 ta, %28, 32;\n"  "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [ta];\n"
+      "add.u32 ta, %28, 64;\n"  "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [ta];\n"
+      "add.u32 ta, %28, 96;\n"  "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [ta];\n"
+      "add.u32 ta, %28, 128;\n" "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [ta];\n"
+      "add.u32 ta, %28, 160;\n" "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [ta];\n"
+      "add.u32 ta, %28, 192;\n" "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24,%25,%26,%27}, [ta];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "}\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27])
+      : "r"(a)
+      : "memory");
+#pragma unroll
+  for (int L = 0; L < 7; ++L)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[L][e] = __uint_as_float(r[4 * L + e]);
+}
+
+// y = 2^(E - 62) S with S = sum_{i=0..6} D_i 256^i (D_i: digit level 4 + i, exact integers below 2^22), as a
+// normalised double-float.  S is formed exactly in 64-bit integer arithmetic (each D_i enters as the bit
+// pattern of D_i + 1.5 * 2^23, the pattern's constant part removed once at the end; all sums wrap modulo
+// 2^64, and S itself fits), then split into 22-bit pieces that convert to float exactly.
+__device__ __forceinline__ dfv levels_to_df(const float (&d)[7], float isc) {
+  uint32_t b[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) b[i] = __float_as_uint(__fadd_rn(d[i], 12582912.0f));
+  constexpr uint64_t kMagic = 0x4B400000ull;
+  constexpr uint64_t kBias = kMagic * (1ull + (1ull << 8) + (1ull << 16) + (1ull << 24) + (1ull << 32) + (1ull << 40) +
+                                       (1ull << 48));
+  const uint32_t top = b[4] + (b[5] << 8) + (b[6] << 16);
+  const uint64_t acc = (uint64_t)b[0] + ((uint64_t)b[1] << 8) + ((uint64_t)b[2] << 16) + ((uint64_t)b[3] << 24) +
+                       ((uint64_t)top << 32) - kBias;
+  const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
+  const uint32_t c0 = lo & 0x3FFFFFu, c1 = __funnelshift_r(lo, hi, 22) & 0x3FFFFFu;
+  const int32_t c2 = (int32_t)hi >> 12;
+  const float f0 = __fadd_rn(__uint_as_float(0x4B000000u | c0), -8388608.0f);
+  const float f1 = __fadd_rn(__uint_as_float(0x4B000000u | c1), -8388608.0f);
+  const float f2 = __fadd_rn(__uint_as_float((uint32_t)(0x4B400000 + c2)), -12582912.0f);
+  float h, e;
+  two_sum(__fmul_rn(f2, 0x1p44f), __fmul_rn(f1, 0x1p22f), h, e);
+  const dfv r = fast_two_sum(h, __fadd_rn(e, f0));
+  return dfv{__fmul_rn(r.h, isc), __fmul_rn(r.l, isc)};
+}
+
+// Chunk exponent of a complex128 chunk in working form: E with 2^E above the chunk's 2-norm (from the high
+// words, with a margin of 2^-8 for the low words and rounding); sets tc.sc = 2^(47 - E), tc.isc = 2^(E - 62).
+// E is clamped to [-80, 100]: amplitudes below 2^-80 are then cut to a few 2^-127.
+__device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, TcCtx &tc) {
+  float part = 0.0f;
+  for (uint32_t o = threadIdx.x; o < nloc; o += kTcThreads) {
+    const float4 v = sm[o];
+    part = __fmaf_rn(v.x, v.x, __fmaf_rn(v.z, v.z, part));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if ((threadIdx.x & 31u) == 0) tc.red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  float tot = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kTcThreads / 32; ++w) tot += tc.red[w];
+  __syncthreads();  // tc.red is reused by the next chunk
+  int E = 0;
+  frexpf(sqrtf(__fmaf_rn(tot, 0x1p-8f, tot)) + 0x1p-126f, &E);
+  E = E < -80 ? -80 : (E > 100 ? 100 : E);
+  tc.sc = __int_as_float((127 + 47 - E) << 23);
+  const int ei = E - 62;
+  tc.isc = ei >= -126 ? __int_as_float((127 + ei) << 23) : __int_as_float(1 << (ei + 149));
+}
+
+// One dense block (GC_BLOCK) on the chunk: every row of the chunk (the 16 amplitudes that differ only in the
+// block's 4 chunk bits) times the block's matrix, D = X W^T.  Pair p writes the A planes of its tiles (each warp
+// group one part), copies the matrix's planes, and one of its threads issues each tile's MMAs as soon as the
+// tile is written (committed to the tile's mbarrier), so the tensor core works on tile t while the pair writes
+// tile t + kTcPairs; then each warp group waits for its tiles and writes its part of the results back.  The
+// CTA synchronises only at the end of the block (the next block's rows mix amplitudes of every tile).
+template <int MODE>
+__device__ __forceinline__ void tc_block(const DevGate &hdr, typename Arith<MODE>::S *sm, int k, TcCtx &tc) {
+  constexpr int planes = MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128;
+  const uint32_t tid = threadIdx.x, g = tid >> 7, pair = g >> 1, h = g & 1u, lane = tid & 127u;
+  const uint32_t R = 1u << (k - kBlockBits), ntiles = R / 128;
+  const unsigned char *src = reinterpret_cast<const unsigned char *>(&hdr) + hdr.gmask;
+  unsigned char *myB = tc.opB + (size_t)pair * planes * kBlockPlaneBytes;
+  int pb[kBlockBits];
+#pragma unroll
+  for (int j = 0; j < kBlockBits; ++j) pb[j] = (int)((hdr.cmask >> (8 * j)) & 0xffu);
+  int ok = tc.ok;
+  if (pair < ntiles) {
+    for (uint32_t u = tid & 255u; u < (uint32_t)(planes * kBlockPlaneBytes / 16); u += 256)
+      cp_async16(myB + 16u * u, src + 16u * u);
+    for (uint32_t t = pair; t < ntiles; t += kTcPairs) {
+      const uint32_t r = t * 128 + lane;
+      const uint32_t b0 = tc_row_base<MODE>(r, pb);
+      unsigned char *row = tc.opA + (r / 8) * 512 + (r % 8) * 16;
+      if constexpr (MODE == MODE_C64_F32) tc_rows_c64(sm, b0, pb, h, row, R);
+      else tc_rows_c128(sm, b0, pb, h, row, R, tc.sc);
+      if (t == pair) cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      pair_sync(pair);
+      if ((tid & 255u) == 0 && ok) tc_issue<MODE>(tc, t, R, myB);
+    }
+    for (uint32_t t = pair; t < ntiles; t += kTcPairs) {
+      if (ok) ok = tc_wait(tc.mbar + t, tc.phase) ? 1 : 0;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t b0 = tc_row_base<MODE>(t * 128 + lane, pb);
+      const uint32_t tl = tc.tmem + ((tid & 96u) << 16);
+      if constexpr (MODE == MODE_C64_F32) {
+        float dv[16];
+        tc_load16(tl + t * kBlockK + h * kBlockDim, dv);
+        if (ok) {
+#pragma unroll
+          for (int s = 0; s < kBlockDim; ++s)
+            reinterpret_cast<float *>(&sm[b0 ^ tc_elem<MODE_C64_F32>(s, pb)])[h] = dv[s];
+        }
+      } else {
+#pragma unroll 1
+        for (uint32_t sg = 0; sg < kBlockDim / 4; ++sg) {
+          float d[7][4];
+          tc_load_levels(tl + t * (7 * kBlockK) + h * kBlockDim + 4u * sg, d);
+          if (ok) {
+            // elements 4 sg .. 4 sg + 3: block bits 0, 1 from e, bits 2, 3 from sg
+            const uint32_t hiofs = tc_elem<MODE_C128_DF32>((int)(4 * sg), pb);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float lv[7];
+#pragma unroll
+              for (int L = 0; L < 7; ++L) lv[L] = d[L][e];
+              const dfv y = levels_to_df(lv, tc.isc);
+              const uint32_t o = b0 ^ hiofs ^ tc_elem<MODE_C128_DF32>(e, pb);
+              reinterpret_cast<float2 *>(&sm[o])[h] = make_float2(y.h, y.l);
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   ok = __syncthreads_and(ok);
   if (tc.ok) tc.phase ^= 1u;
   if (!ok && tc.ok && tid == 0) atomicOr(tc.err, 1u);
   tc.ok = ok;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // Read back: warp w reads TMEM lanes 32 (w % 4) ..; warp group g = w / 4 takes tiles g, g + 2, ...
-  const uint32_t lane = tid & 127u, group = tid >> 7;
-  for (uint32_t t = group; t < ntiles; t += kFusedThreads / 128) {
-    float dv[32];
-    tc_load32(tc.tmem + ((tid & 96u) << 16) + t * kBlockK, dv);
-    if (ok) {
-      uint32_t b0;
-      tc_row_slots<MODE_C64_F32>(t * 128 + lane, pb, b0);
-#pragma unroll
-      for (int s = 0; s < kBlockDim; ++s) sm[b0 ^ xo[s]] = make_float2(dv[s], dv[kBlockDim + s]);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
 }
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
 // permuted store's table.
-template <int MODE, bool PACK = true, bool TC = false>
+template <int MODE, bool PACK = true, bool TC = false, int NT = kFusedThreads>
 __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, typename Arith<MODE>::S *sm,
                                             uint64_t *rowoff, TcCtx *tc = nullptr) {
   using M = Arith<MODE>;
@@ -515,7 +711,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     base = ((base >> q) << (q + 1)) | (base & ((1ull << q) - 1ull));
   }
   // Row offsets: row r's bits go to qpos[c..k-1].
-  for (uint32_t r = tid; r < nrows; r += kFusedThreads) {
+  for (uint32_t r = tid; r < nrows; r += NT) {
     uint64_t off = 0;
     for (int j = c; j < k; ++j) off |= (uint64_t)((r >> (j - c)) & 1u) << p.qpos[j];
     rowoff[r] = off;
@@ -536,13 +732,13 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const bool mine = (p.init_x & ~p.qmask) == base;
     uint32_t lx = 0;
     for (int j = 0; j < k; ++j) lx |= (uint32_t)((p.init_x >> p.qpos[j]) & 1ull) << j;
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads) sm[slot<MODE>(o)] = (mine && o == lx) ? M::one() : M::zero();
+    for (uint32_t o = tid; o < nloc; o += NT) sm[slot<MODE>(o)] = (mine && o == lx) ? M::one() : M::zero();
   } else {
     // The whole chunk in flight at once: one 16-byte asynchronous copy per amplitude (complex128) or per
     // adjacent pair (complex64), straight into its shared-memory slot.  Rows are 2^c >= 2 amplitudes long
     // and 16-byte aligned, so a pair never straddles two rows.
     constexpr uint32_t per = 16u / sizeof(G);
-    for (uint32_t u = tid; u < nloc / per; u += kFusedThreads) {
+    for (uint32_t u = tid; u < nloc / per; u += NT) {
       const uint32_t o = u * per;
       cp_async16(&sm[slot<MODE>(o)], &psi[base + rowoff[o >> c] + (o & lowmask)]);
     }
@@ -550,15 +746,16 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     if constexpr (MODE == MODE_C128_DF32) {
       // Each thread converts the slots it copied, in place (double2 and the float4 working form are both
       // 16 bytes), so no barrier is needed before the conversion.
-      for (uint32_t o = tid; o < nloc; o += kFusedThreads) sm[o] = M::load(((const G *)sm)[o]);
+      for (uint32_t o = tid; o < nloc; o += NT) sm[o] = M::load(((const G *)sm)[o]);
     }
   }
   __syncthreads();
+  if constexpr (TC && MODE == MODE_C128_DF32) tc_chunk_scale(sm, nloc, *tc);
 
   for (int gi = 0; gi < p.ngates; ++gi) {
     const DevGate &g = p.gates[gi];
     if (g.cls == GC_BLOCK) {  // its gmask is the offset of its operand planes, not a control mask
-      if constexpr (TC && MODE == MODE_C64_F32) tc_block_c64(g, sm, k, *tc);
+      if constexpr (TC) tc_block<MODE>(g, sm, k, *tc);
       continue;
     }
     const uint64_t gmask = g.gmask;
@@ -566,14 +763,14 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const uint32_t cls = g.cls;
     if (cls == GC_ROW) continue;  // consumed with its GC_DENSE4 record
     if (cls == GC_DENSE4) {
-      chunk_quads<MODE>(sm, p.gates + gi, nloc >> 2, g.target, (int)g.tmask, (uint32_t)g.cmask);
+      chunk_quads<MODE, NT>(sm, p.gates + gi, nloc >> 2, g.target, (int)g.tmask, (uint32_t)g.cmask);
       gi += 3;
       __syncthreads();
       continue;
     }
     if (cls == GC_CUBE) {
       if constexpr (MODE == MODE_C64_F32) {
-        cube_run<kCubeBits>(p.gates + gi + 1, g.target, g.cmask, base, sm, k);
+        cube_run<kCubeBits, NT>(p.gates + gi + 1, g.target, g.cmask, base, sm, k);
         gi += g.target;
         __syncthreads();
       }
@@ -588,17 +785,17 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
       if (cls == GC_PHASE) {
         // Only the amplitudes with the target and every local control bit set.
         const uint32_t fix = tb | cm, cnt = nloc >> __popc(fix);
-        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+        for (uint32_t i = tid; i < cnt; i += NT) {
           const uint32_t j = expand_fixed(i, fix, fix);
           sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
         }
       } else {
         // One loop per class, so the class test is not inside the pair loop.
         switch (cls) {
-          case GC_GENERAL: chunk_pairs<MODE, GC_GENERAL, PACK>(sm, cf, half, t, tb, cm); break;
-          case GC_DIAG: chunk_pairs<MODE, GC_DIAG, PACK>(sm, cf, half, t, tb, cm); break;
-          case GC_ANTIDIAG: chunk_pairs<MODE, GC_ANTIDIAG, PACK>(sm, cf, half, t, tb, cm); break;
-          default: chunk_pairs<MODE, GC_X, PACK>(sm, cf, half, t, tb, cm); break;
+          case GC_GENERAL: chunk_pairs<MODE, GC_GENERAL, PACK, NT>(sm, cf, half, t, tb, cm); break;
+          case GC_DIAG: chunk_pairs<MODE, GC_DIAG, PACK, NT>(sm, cf, half, t, tb, cm); break;
+          case GC_ANTIDIAG: chunk_pairs<MODE, GC_ANTIDIAG, PACK, NT>(sm, cf, half, t, tb, cm); break;
+          default: chunk_pairs<MODE, GC_X, PACK, NT>(sm, cf, half, t, tb, cm); break;
         }
       }
     } else {
@@ -608,12 +805,12 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
       // index stays a constant, so the coefficients stay in registers).
       const uint32_t cnt = nloc >> __popc(cm);
       if (one) {
-        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+        for (uint32_t i = tid; i < cnt; i += NT) {
           const uint32_t j = expand_fixed(i, cm, cm);
           sm[slot<MODE>(j)] = M::cmul(cf, 3, sm[slot<MODE>(j)]);
         }
       } else if (cls != GC_PHASE) {
-        for (uint32_t i = tid; i < cnt; i += kFusedThreads) {
+        for (uint32_t i = tid; i < cnt; i += NT) {
           const uint32_t j = expand_fixed(i, cm, cm);
           sm[slot<MODE>(j)] = M::cmul(cf, 0, sm[slot<MODE>(j)]);
         }
@@ -623,15 +820,15 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
   }
 
   if (!p.permuted) {
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads)
+    for (uint32_t o = tid; o < nloc; o += NT)
       psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(o)]);
   } else {
     // Store with chunk-local bit j sent to physical bit qpos_out[j]: output slot o (bits in the ascending
     // order of Q) takes local amplitude P(o), bit j of P(o) = bit src_bit[j] of o.
     uint32_t plo = 0;
-    for (int j = 0; j < k; ++j) plo |= ((tid >> p.src_bit[j]) & 1u) << j;
+    for (int j = 0; j < k; ++j) plo |= (((tid & 255u) >> p.src_bit[j]) & 1u) << j;  // P(o mod 256), NT % 256 == 0
     const uint32_t *ptab = (const uint32_t *)(rowoff + nrows);
-    for (uint32_t o = tid; o < nloc; o += kFusedThreads)
+    for (uint32_t o = tid; o < nloc; o += NT)
       psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(plo | ptab[o >> 8])]);
   }
   __syncthreads();
@@ -650,7 +847,7 @@ __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused(con
 // columns for the CTA's accumulators (ncols * CTAs per SM <= 512, so the allocation never waits on a CTA of
 // this launch), thread 0 initialises the mbarrier the MMAs commit to; both are released at the end.
 template <int MODE>
-__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_tc(const PassDesc p, uint64_t nchunks, uint32_t ncols,
+__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, uint64_t nchunks, uint32_t ncols,
                                                                unsigned *err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   using S = typename Arith<MODE>::S;
@@ -660,15 +857,16 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_tc(const PassDesc p,
   TcCtx tc;
   tc.opA = smraw + tc_smem_base<MODE>(p.k);
   tc.opB = tc.opA + (size_t)tc_planes<MODE>() * R * kTcRowBytes;
-  tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)tc_planes<MODE>() * kBlockPlaneBytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(tc.mbar + 1);
+  tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)kTcPairs * tc_planes<MODE>() * kBlockPlaneBytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tc.mbar + kTcMaxTiles);
+  tc.red = reinterpret_cast<float *>(tc.mbar + kTcMaxTiles + 1);
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)), "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(tc.mbar)) : "memory");
+  if (threadIdx.x < kTcMaxTiles) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(tc.mbar + threadIdx.x)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -678,7 +876,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_tc(const PassDesc p,
   tc.phase = 0;
   tc.ok = 1;
   tc.err = err;
-  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) fused_chunk<MODE, true, true>(p, ch, sm, rowoff, &tc);
+  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
+    fused_chunk<MODE, true, true, kTcThreads>(p, ch, sm, rowoff, &tc);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x < 32)
@@ -885,7 +1084,7 @@ cudaError_t tc_launch(const PassDesc &p, cudaStream_t st, FusedSched *sched) {
   cudaError_t e = ensure_smem((const void *)k_fused_tc<MODE>, smem, granted);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_tc<MODE>, kFusedThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_tc<MODE>, kTcThreads, smem);
   if (occ < 1) occ = 1;
   const uint32_t tiles = 1u << (p.k - kBlockBits - 7);
   const uint32_t levels = MODE == MODE_C64_F32 ? 1u : 7u;
@@ -896,7 +1095,7 @@ cudaError_t tc_launch(const PassDesc &p, cudaStream_t st, FusedSched *sched) {
   const uint64_t nchunks = 1ull << (p.n - p.k);
   const uint64_t cap = (uint64_t)sms() * occ;
   const unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
-  k_fused_tc<MODE><<<grid, kFusedThreads, smem, st>>>(p, nchunks, ncols, &sched->tc_err);
+  k_fused_tc<MODE><<<grid, kTcThreads, smem, st>>>(p, nchunks, ncols, &sched->tc_err);
   return cudaGetLastError();
 }
 
@@ -907,6 +1106,7 @@ cudaError_t launch_fused(const PassDesc &p, int mode, cudaStream_t st, int f64_s
     // scratch that carries its error word
     if (sched == nullptr || p.k < kBlockBits + 7 || p.k > 13) return cudaErrorInvalidValue;
     if (mode == MODE_C64_F32) return tc_launch<MODE_C64_F32>(p, st, sched);
+    if (mode == MODE_C128_DF32) return tc_launch<MODE_C128_DF32>(p, st, sched);
     return cudaErrorInvalidValue;
   }
   if (mode == MODE_C128_DF32 && f64_share > 0 && f64_share < 100 && sched != nullptr) {

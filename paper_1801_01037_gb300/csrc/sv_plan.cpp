@@ -581,7 +581,7 @@ static void make_plan_records(int n, const PlanConfig &cfg, std::vector<int> &pe
       ++ng;
     }
     d.nblocks = 0;
-    if (cfg.block_mode >= 0 && k >= 11 && ng > 1) {
+    if (cfg.block_mode >= 0 && k >= kBlockBits + 7 && k <= (cfg.block_mode == MODE_C64_F32 ? 13 : 12) && ng > 1) {
       const size_t first = P.pass_gate_offset.back();
       std::vector<DevGate> run(P.fused_gates.begin() + first, P.fused_gates.end());
       const int nb = group_blocks(run, k, cfg.block_mode, cfg.block_min_cost, P.block_data);

@@ -21,9 +21,11 @@ def built():
     B.load()
 
 
-def run(n, gates, dtype, blocks, chunk_k=0, x0=0, graph=False):
+def run(n, gates, dtype, blocks, chunk_k=0, x0=0, graph=False, arith=B.SV_ARITH_AUTO):
     h = B.sv_create(n, dtype)
     try:
+        if dtype == B.SV_C128:
+            B.sv_set_option(h, B.SV_OPT_ARITH, arith)
         B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1 if blocks else 0)
         if chunk_k:
             B.sv_set_option(h, B.SV_OPT_CHUNK_QUBITS, chunk_k)
@@ -95,11 +97,73 @@ def test_tensor_blocks_in_a_captured_graph_and_deep_circuit():
     assert np.array_equal(got, again), "blocks are deterministic and the graph replays the same launches"
 
 
-def test_tensor_blocks_are_ignored_below_one_tile_and_for_complex128():
-    # chunks of fewer than 2^11 amplitudes (a 128-row tile) and complex128 states keep the per-gate path
+def test_tensor_blocks_are_ignored_where_they_do_not_apply():
+    # chunks of fewer than 2^11 amplitudes (a 128-row tile), complex128 with native FP64 arithmetic, and
+    # complex128 chunks of 2^13 amplitudes keep the per-gate path
     w = C.random_workload(10, 3, seed=9)
     got, st = run(10, w.gates, B.SV_C64, True)
     assert st["blocks"] == 0
     assert_close(got, run_oracle(10, w.gates), B.SV_C64, "n=10")
-    got, st = run(14, C.random_workload(14, 2, seed=9).gates, B.SV_C128, True)
+    w = C.random_workload(14, 2, seed=9)
+    got, st = run(14, w.gates, B.SV_C128, True, arith=B.SV_ARITH_F64)
     assert st["blocks"] == 0
+    assert_close(got, run_oracle(14, w.gates), B.SV_C128, "n=14 FP64")
+    got, st = run(14, w.gates, B.SV_C128, True, chunk_k=13)
+    assert st["blocks"] == 0
+
+
+# ---- complex128: exact digit products ------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,chunk_k", [(11, 11), (12, 11), (12, 12), (13, 12), (15, 11), (17, 12), (20, 12)])
+def test_c128_random_layers_on_tensor_cores_match_oracle(n, chunk_k):
+    w = C.random_workload(n, 4, seed=600 + n)
+    got, st = run(n, w.gates, B.SV_C128, True, chunk_k)
+    assert st["blocks"] > 0 and st["block_gates"] >= 2 * st["blocks"], st
+    want = run_oracle(n, w.gates)
+    assert_close(got, want, B.SV_C128, f"c128 n={n} k={chunk_k} tensor blocks")
+    per_gate, _ = run(n, w.gates, B.SV_C128, False, chunk_k)
+    assert_close(got, per_gate, B.SV_C128, "c128 tensor blocks vs double-float per gate")
+
+
+@pytest.mark.parametrize("n,chunk_k", [(12, 12), (16, 11), (18, 12)])
+def test_c128_mixed_gate_families_on_tensor_cores(n, chunk_k):
+    rng = np.random.Generator(np.random.PCG64(177 + n))
+    gates = mixed_circuit(n, rng)
+    got, st = run(n, gates, B.SV_C128, True, chunk_k)
+    assert st["blocks"] > 0, st
+    assert_close(got, run_oracle(n, gates), B.SV_C128, f"c128 mixed n={n}")
+
+
+def test_c128_qft_and_deep_circuit_on_tensor_cores():
+    w = C.qft_random_workload(16, 3, seed=15)
+    got, st = run(16, w.gates, B.SV_C128, True, 12, x0=w.x0)
+    assert st["blocks"] > 0, st
+    assert_close(got, run_oracle(16, w.gates, x0=w.x0), B.SV_C128, "c128 qft + layers")
+    n = 22
+    w = C.random_workload(n, 12, seed=2025)
+    got, st = run(n, w.gates, B.SV_C128, True, 12, graph=True)
+    assert st["blocks"] > 0, st
+    assert_close(got, run_oracle(n, w.gates), B.SV_C128, "c128 graph, 12 layers, n=22")
+    again, _ = run(n, w.gates, B.SV_C128, True, 12)
+    assert np.array_equal(got, again)
+
+
+def test_c128_tensor_blocks_on_small_and_unnormalised_states():
+    # a whole-state chunk (n = k = 11, 2-norm 1) through many blocks, and a state scaled far from norm 1
+    n = 11
+    w = C.random_workload(n, 30, seed=7)
+    got, st = run(n, w.gates, B.SV_C128, True, 11)
+    assert st["blocks"] > 20, st
+    assert_close(got, run_oracle(n, w.gates), B.SV_C128, "c128 n=11, 30 layers")
+    psi0 = C.random_state(12, seed=8) * 2.0 ** -40
+    h = B.sv_create(12, B.SV_C128)
+    try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1)
+        B.sv_write_amplitudes(h, 0, psi0)
+        g = C.random_workload(12, 3, seed=10).gates
+        B.sv_apply_circuit(h, g)
+        got = B.sv_read_amplitudes(h)
+    finally:
+        B.sv_destroy(h)
+    want = run_oracle(12, g, psi0)
+    assert np.max(np.abs(got - want)) <= 1e-12 * 2.0 ** -40
