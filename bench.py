@@ -306,12 +306,13 @@ def run_ours(args):
         amps = B.sv_read_amplitudes(h, 0, READ_COUNT)
         return nrm, amps
 
-    # Chunk size per dtype from the autotuner, timed on a 4-layer circuit of the same shape (untimed here).
+    # Chunk size, FP64 share and tensor blocks per dtype from the autotuner, timed on an 8-layer circuit of the
+    # same shape (another seed; untimed here).
     chunk_k, tuning, tensor_blocks = {}, {}, {}
     f64_share = B.SV_F64_SHARE_DEFAULT  # share of chunks done on the FP64 pipe unless the autotuner picks one
     if not args.no_autotune:
         from paper_1801_01037_gb300 import autotune
-        probe = C.random_workload(args.n, 4, seed=SEED + 7).gates
+        probe = C.random_workload(args.n, 8, seed=SEED + 7).gates
         for dt, ar in ((B.SV_C128, B.SV_ARITH_DF32), (B.SV_C64, B.SV_ARITH_AUTO)):
             res = autotune.tune(args.n, dt, probe, ar, save=False)
             chunk_k[dt] = res["best"]

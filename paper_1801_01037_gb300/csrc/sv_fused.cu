@@ -357,6 +357,7 @@ constexpr int kTcThreads = 512;
 constexpr int kTcGroups = kTcThreads / 128;
 constexpr int kTcPairs = kTcGroups / 2;
 constexpr int kTcMaxTiles = 4;                    // 2^13-amplitude chunks: 512 rows
+constexpr int kTcGateCopy = 64;                   // gate records staged in shared memory per pass
 
 // Per-CTA state of the tensor-core pass (the same in every thread).
 struct TcCtx {
@@ -625,11 +626,12 @@ __device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, 
 // tile t + kTcPairs; then each warp group waits for its tiles and writes its part of the results back.  The
 // CTA synchronises only at the end of the block (the next block's rows mix amplitudes of every tile).
 template <int MODE>
-__device__ __forceinline__ void tc_block(const DevGate &hdr, typename Arith<MODE>::S *sm, int k, TcCtx &tc) {
+__device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr, typename Arith<MODE>::S *sm, int k,
+                                         TcCtx &tc) {
   constexpr int planes = MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128;
   const uint32_t tid = threadIdx.x, g = tid >> 7, pair = g >> 1, h = g & 1u, lane = tid & 127u;
   const uint32_t R = 1u << (k - kBlockBits), ntiles = R / 128;
-  const unsigned char *src = reinterpret_cast<const unsigned char *>(&hdr) + hdr.gmask;
+  const unsigned char *src = reinterpret_cast<const unsigned char *>(ghdr) + hdr.gmask;  // offset from the blob record
   unsigned char *myB = tc.opB + (size_t)pair * planes * kBlockPlaneBytes;
   int pb[kBlockBits];
 #pragma unroll
@@ -695,7 +697,9 @@ __device__ __forceinline__ void tc_block(const DevGate &hdr, typename Arith<MODE
 // permuted store's table.
 template <int MODE, bool PACK = true, bool TC = false, int NT = kFusedThreads>
 __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, typename Arith<MODE>::S *sm,
-                                            uint64_t *rowoff, TcCtx *tc = nullptr) {
+                                            uint64_t *rowoff, TcCtx *tc = nullptr, const DevGate *gcopy = nullptr) {
+  // gate records: the pass's array in global memory, or a copy of it in shared memory (same order)
+  const DevGate *const GR = gcopy ? gcopy : p.gates;
   using M = Arith<MODE>;
   using G = typename M::G;
   using S = typename M::S;
@@ -753,9 +757,9 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
   if constexpr (TC && MODE == MODE_C128_DF32) tc_chunk_scale(sm, nloc, *tc);
 
   for (int gi = 0; gi < p.ngates; ++gi) {
-    const DevGate &g = p.gates[gi];
+    const DevGate &g = GR[gi];
     if (g.cls == GC_BLOCK) {  // its gmask is the offset of its operand planes, not a control mask
-      if constexpr (TC) tc_block<MODE>(g, sm, k, *tc);
+      if constexpr (TC) tc_block<MODE>(g, p.gates + gi, sm, k, *tc);
       continue;
     }
     const uint64_t gmask = g.gmask;
@@ -763,14 +767,14 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     const uint32_t cls = g.cls;
     if (cls == GC_ROW) continue;  // consumed with its GC_DENSE4 record
     if (cls == GC_DENSE4) {
-      chunk_quads<MODE, NT>(sm, p.gates + gi, nloc >> 2, g.target, (int)g.tmask, (uint32_t)g.cmask);
+      chunk_quads<MODE, NT>(sm, GR + gi, nloc >> 2, g.target, (int)g.tmask, (uint32_t)g.cmask);
       gi += 3;
       __syncthreads();
       continue;
     }
     if (cls == GC_CUBE) {
       if constexpr (MODE == MODE_C64_F32) {
-        cube_run<kCubeBits, NT>(p.gates + gi + 1, g.target, g.cmask, base, sm, k);
+        cube_run<kCubeBits, NT>(GR + gi + 1, g.target, g.cmask, base, sm, k);
         gi += g.target;
         __syncthreads();
       }
@@ -876,8 +880,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, ui
   tc.phase = 0;
   tc.ok = 1;
   tc.err = err;
+  // The pass's gate records, copied once to shared memory (every chunk reads each of them); a pass with more
+  // than kTcGateCopy records reads them from global memory.
+  DevGate *gcopy = nullptr;
+  if (p.ngates <= kTcGateCopy) {
+    gcopy = reinterpret_cast<DevGate *>(smraw + tc_smem_bytes<MODE>(p.k));
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.gates);
+    uint4 *dst = reinterpret_cast<uint4 *>(gcopy);
+    for (uint32_t u = threadIdx.x; u < (uint32_t)p.ngates * (sizeof(DevGate) / 16); u += kTcThreads) dst[u] = src[u];
+    __syncthreads();
+  }
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
-    fused_chunk<MODE, true, true, kTcThreads>(p, ch, sm, rowoff, &tc);
+    fused_chunk<MODE, true, true, kTcThreads>(p, ch, sm, rowoff, &tc, gcopy);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x < 32)
@@ -1079,7 +1093,7 @@ int fused_smem_bytes(int mode, int k) {
 
 template <int MODE>
 cudaError_t tc_launch(const PassDesc &p, cudaStream_t st, FusedSched *sched) {
-  const int smem = tc_smem_bytes<MODE>(p.k);
+  const int smem = tc_smem_bytes<MODE>(p.k) + (p.ngates <= kTcGateCopy ? p.ngates * (int)sizeof(DevGate) : 0);
   static std::atomic<int> granted[64] = {};
   cudaError_t e = ensure_smem((const void *)k_fused_tc<MODE>, smem, granted);
   if (e != cudaSuccess) return e;
