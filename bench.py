@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=100, help="requests of the served sample in the default line")
     ap.add_argument("--no-extra", action="store_true", help="skip the served and batched samples of the default line")
     ap.add_argument("--no-n33", action="store_true", help="skip the n = 33 single-gate sweep")
+    ap.add_argument("--tensor-blocks", type=int, default=None,
+                    help="force SV_OPT_TENSOR_BLOCKS for both dtypes instead of the autotuner's choice")
     return ap.parse_args()
 
 
@@ -320,6 +322,8 @@ def run_ours(args):
             tuning["c128" if dt == B.SV_C128 else "c64"] = res
             if dt == B.SV_C128:
                 f64_share = int(res["best_f64_share"])
+    if args.tensor_blocks is not None:
+        tensor_blocks = {B.SV_C128: args.tensor_blocks, B.SV_C64: args.tensor_blocks}
 
     def timed(dtype, arith, steps, warmup, profile=False, sampler=None, renorm=0):
         h = B.sv_create(args.n, dtype)
@@ -450,7 +454,7 @@ def run_ours(args):
     f64_fma_launch = f64_fmas_per_step(kernel_gates, args.n) * (f64_share / 100.0) / max(1, c128["stats"]["passes"])
     f64_peak = 152 * 1.73 * sm_hz * 1e6 / 1e12  # measured FP64 multiply-adds per clock per SM
     f64_achieved = f64_fma_launch / (avg_ms * 1e-3) / 1e12 if c128["fused_launches"] else None
-    traffic = committed_traffic(args.n)
+    traffic = committed_traffic(args.n, "k_fused_tc" if c128["stats"]["blocks"] else "k_fused_mixed")
     # init, passes, sweeps, bit-permutation passes, the two norm kernels, and the two product-start kernels
     folded_start = c128["stats"]["absorbed"] > 0
     launches_per_step = (1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
@@ -650,12 +654,12 @@ def f64_fmas_per_step(gates, n):
     return f
 
 
-def committed_traffic(n):
-    """DRAM bytes per launch of the fused c128 pass on n qubits, scaled from the committed ncu capture (a pass
-    reads and writes the whole state once, so traffic is proportional to 2^n), if that capture still matches
-    the kernel source (null otherwise)."""
+def committed_traffic(n, kernel="k_fused_mixed"):
+    """DRAM bytes per launch of a fused c128 pass kernel on n qubits, scaled from the committed ncu capture at
+    n = 28 (a pass reads and writes the whole state once, so traffic is proportional to 2^n), if that capture
+    still matches the kernel source (null otherwise)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fused_c128_df32_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "fused_c128_traffic_n28.txt")
     try:
         kv = dict(line.split("=", 1) for line in open(path).read().split() if "=" in line)
         h = hashlib.sha256()
@@ -663,7 +667,7 @@ def committed_traffic(n):
             h.update(open(os.path.join(ROOT, "paper_1801_01037_gb300", "csrc", f), "rb").read())
         if kv.get("source_sha256") != h.hexdigest()[:16]:
             return None
-        return float(kv["bytes_per_full_launch_n27"]) * 2.0 ** (n - 27)
+        return float(kv[kernel + "_bytes_n28"]) * 2.0 ** (n - 28)
     except Exception:
         return None
 
