@@ -134,7 +134,8 @@ void real_form(const double *U, double (*W)[kBlockK]) {
 
 // Operand planes of a block.  complex64: three bfloat16 planes w = w0 + w1 + w2 (each the rounding of what
 // the planes before it leave, so the sum holds 24 bits of w).  complex128: six planes of balanced base-256
-// digits of round(w * 2^47) (each in [-128, 128), exact in bfloat16), digit 0 the least significant.
+// digits of round(w * 2^47) (each in [-128, 128), the top one in [-128, 128] so that |w| = 1 is exact; all
+// exact in bfloat16), digit 0 the least significant.
 void encode_planes(int mode, const double (*W)[kBlockK], unsigned char *dst) {
   const int planes = mode == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128;
   std::memset(dst, 0, planes * kBlockPlaneBytes);
