@@ -73,8 +73,9 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=100, help="requests of the served sample in the default line")
     ap.add_argument("--no-extra", action="store_true", help="skip the served and batched samples of the default line")
     ap.add_argument("--no-n33", action="store_true", help="skip the n = 33 single-gate sweep")
-    ap.add_argument("--tensor-blocks", type=int, default=None,
-                    help="force SV_OPT_TENSOR_BLOCKS for both dtypes instead of the autotuner's choice")
+    ap.add_argument("--tensor-blocks", default=None,
+                    help="force SV_OPT_TENSOR_BLOCKS instead of the autotuner's choice: one value for both dtypes, "
+                         "or 'C128,C64'")
     return ap.parse_args()
 
 
@@ -323,7 +324,8 @@ def run_ours(args):
             if dt == B.SV_C128:
                 f64_share = int(res["best_f64_share"])
     if args.tensor_blocks is not None:
-        tensor_blocks = {B.SV_C128: args.tensor_blocks, B.SV_C64: args.tensor_blocks}
+        tb = [int(v) for v in str(args.tensor_blocks).split(",")]
+        tensor_blocks = {B.SV_C128: tb[0], B.SV_C64: tb[-1]}
 
     def timed(dtype, arith, steps, warmup, profile=False, sampler=None, renorm=0):
         h = B.sv_create(args.n, dtype)
@@ -461,7 +463,7 @@ def run_ours(args):
                          + (2 if folded_start else 0))
     # The other configurations of the metric, measured after the timed region: a bounded served stream
     # (complex64, 150 GB budget) and a 512-circuit batch per dtype (chunk sizes per size class of n).
-    served = batched = None
+    served = batched = qft = None
     if not args.no_extra:
         served = served_measure(B, args.served_rate, args.served_requests)
         ws_b = C.batched_workloads(512, seed=1004)
@@ -470,6 +472,12 @@ def run_ours(args):
             ks, picked = batch_chunk_sizes(B, [w.n for w in ws_b], dt_b, not args.no_autotune)
             batched[name] = {**batched_measure(B, ws_b, dt_b, ks), "chunk_qubits": picked or "default"}
         batched["workload"] = "512 random circuits, n log-uniform in [10, 22], 10-40 layers, seed 1004"
+        qft = {"qft20": qft_measure(B, "qft20", 5, 3)}
+        if args.n == N_QUBITS and not args.no_n33:
+            import torch
+            free_b, _ = torch.cuda.mem_get_info()
+            if free_b >= (16 << 33) + (2 << 30):
+                qft["qft33"] = qft_measure(B, "qft33", 1, 1)
     # c64 with periodic renormalisation (every RENORM_PERIOD gates), one step, for its cost beside c64 without
     c64_renorm = timed(B.SV_C64, B.SV_ARITH_AUTO, 1, 1, renorm=RENORM_PERIOD)
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
@@ -514,6 +522,7 @@ def run_ours(args):
         "effective_hbm_gbs": value * 2 * state_bytes / 1e9 / WORLD,
         "served": served,
         "batched": batched,
+        "qft": qft,
         "plan": {"passes_per_step": c128["stats"]["passes"], "sweeps_per_step": c128["stats"]["sweep_gates"],
                  "fused_gates_per_step": c128["stats"]["fused_gates"],
                  "folded_into_product_start": c128["stats"]["absorbed"],
@@ -672,16 +681,12 @@ def committed_traffic(n, kernel="k_fused_mixed"):
         return None
 
 
-def run_single_config(args):
-    """The other single-state configurations, complex128, default options (autotuned chunk size not applied):
-    qft20 = QFT on n = 20 from a seeded basis state (seed 1001, 16 MiB state, L2-resident: launch overhead and
-    graph replay matter); qft33 = QFT on n = 33 then 10 random layers (seed 1003, 128 GiB state)."""
+def qft_measure(B, which, steps, warmup):
+    """qft20 = QFT on n = 20 from a seeded basis state (seed 1001, 16 MiB state, L2-resident: launch overhead and
+    graph replay matter); qft33 = QFT on n = 33 then 10 random layers (seed 1003, 128 GiB state).  complex128,
+    library defaults; a step = init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back."""
     import torch
-    from paper_1801_01037_gb300 import build as sv_build
-    sv_build.build()
-    from paper_1801_01037_gb300 import _binding as B
-    B.load()
-    w = C.qft_workload(20, seed=1001) if args.workload == "qft20" else C.qft_random_workload(33, 10, seed=1003)
+    w = C.qft_workload(20, seed=1001) if which == "qft20" else C.qft_random_workload(33, 10, seed=1003)
     h = B.sv_create(w.n, B.SV_C128)
     try:
         def step():
@@ -689,26 +694,34 @@ def run_single_config(args):
             B.sv_apply_circuit_graph(h, w.gates)
             B.sv_norm(h)
             B.sv_read_amplitudes(h, 0, READ_COUNT)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         st = B.sv_last_plan_stats(h)
     finally:
         B.sv_destroy(h)
     G = len(w.gates)
-    print(json.dumps({"metric": f"gates/s, {w.name}, complex128", "value": G / (ms / 1e3), "unit": "gates/s",
-                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "gates": G, "n": w.n,
-                      "effective_hbm_gbs": G / (ms / 1e3) * 2 * (16 << w.n) / 1e9,
-                      "plan": {"passes": st["passes"], "sweeps": st["sweep_gates"], "relabels": st["relabels"]},
-                      "step": "init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back"}),
-          flush=True)
+    return {"metric": f"gates/s, {w.name}, complex128", "value": G / (ms / 1e3), "unit": "gates/s",
+            "ms_per_step": ms, "steps": steps, "warmup": warmup, "gates": G, "n": w.n,
+            "effective_hbm_gbs": G / (ms / 1e3) * 2 * (16 << w.n) / 1e9,
+            "plan": {"passes": st["passes"], "sweeps": st["sweep_gates"], "relabels": st["relabels"]},
+            "step": "init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back"}
+
+
+def run_single_config(args):
+    """The other single-state configurations (see qft_measure), as their own JSON line."""
+    from paper_1801_01037_gb300 import build as sv_build
+    sv_build.build()
+    from paper_1801_01037_gb300 import _binding as B
+    B.load()
+    print(json.dumps(qft_measure(B, args.workload, args.steps, args.warmup)), flush=True)
 
 
 SIZE_CLASSES = ((0, 13), (14, 17), (18, 99))

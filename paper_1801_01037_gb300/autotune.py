@@ -47,7 +47,7 @@ def save_cache(cache: dict) -> None:
 
 
 F64_SHARES = (0, 10, 12, 14, 16, 18, 20)
-TENSOR_BLOCKS = (0, 4, 6)
+TENSOR_BLOCKS = (0, 3, 4, 6)
 
 
 def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1,
@@ -96,7 +96,7 @@ def tune(n: int, dtype: int, gates, arith: int = B.SV_ARITH_AUTO, candidates=Non
         res["best_f64_share"] = share
         res["f64_share_ms"] = {str(s): v for s, v in sh.items()}
     if arith != B.SV_ARITH_F64:
-        # dense tensor-core blocks (off, or blocks that replace at least 4 or 6 dense one-qubit updates)
+        # dense tensor-core blocks (off, or blocks that replace at least 3, 4 or 6 dense one-qubit updates)
         tb = {t: time_candidate(n, dtype, arith, gates, best, f64_share=share, tensor_blocks=t) for t in TENSOR_BLOCKS}
         res["best_tensor_blocks"] = min(tb, key=tb.get)
         res["tensor_blocks_ms"] = {str(t): v for t, v in tb.items()}

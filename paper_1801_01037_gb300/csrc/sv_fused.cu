@@ -301,9 +301,10 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
          (1ull << 46);
 }
 // Instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), bfloat16 A and B (bits 7-9, 10-12 = 1),
-// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBlockK >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128; N a multiple of 16 up to 256).
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 constexpr int kTcRowBytes = kBlockK * 2;          // one row of one plane
 constexpr int kTcTileBytes = 128 * kTcRowBytes;   // 128 rows of one plane
 constexpr uint64_t kTcWaitNs = 2000000000ull;     // bound of one wait for the tensor cores
@@ -321,15 +322,18 @@ template <int MODE>
 __host__ __device__ constexpr int tc_planes() { return MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128; }
 template <int MODE>
 __host__ __device__ constexpr int tc_smem_base(int k) { return (smem_bytes<MODE>(k) + 1023) & ~1023; }
+// B planes per pair: complex128 keeps a zero plane in front of the block's six digit planes (see tc_issue).
+template <int MODE>
+__host__ __device__ constexpr int tc_bplanes() { return MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128 + 1; }
 template <int MODE>
 __host__ __device__ constexpr int tc_smem_bytes(int k) {
   return tc_smem_base<MODE>(k) + tc_planes<MODE>() * ((1 << (k - kBlockBits)) * kTcRowBytes) +
-         2 * tc_planes<MODE>() * (int)kBlockPlaneBytes + 256;
+         2 * tc_bplanes<MODE>() * (int)kBlockPlaneBytes + 256;
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               ::"r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+               ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
                : "memory");
 }
 
@@ -362,7 +366,7 @@ constexpr int kTcGateCopy = 64;                   // gate records staged in shar
 // Per-CTA state of the tensor-core pass (the same in every thread).
 struct TcCtx {
   unsigned char *opA;   // A planes: plane-major, rows x kTcRowBytes each
-  unsigned char *opB;   // B planes, one set per pair (kTcPairs x planes x kBlockPlaneBytes)
+  unsigned char *opB;   // B planes, one set per pair (kTcPairs x tc_bplanes x kBlockPlaneBytes)
   uint64_t *mbar;       // one mbarrier per tile
   uint32_t tmem;        // TMEM address of this CTA's accumulators (lane 0, first column)
   uint32_t phase;       // parity of the next phase of every tile's mbarrier
@@ -370,6 +374,7 @@ struct TcCtx {
   unsigned *err;        // global error word
   float *red;           // kTcThreads / 32 floats of shared scratch (complex128 chunk norm)
   float sc, isc;        // complex128: 2^(47 - E) and 2^(E - 62) for the current chunk's exponent E
+  int fixed_in;         // complex128: the chunk holds the previous block's output in fixed point (see below)
 };
 
 // Row r's base slot (its index with zeros at the block bits, through the slot map).
@@ -402,8 +407,15 @@ __device__ __forceinline__ void pair_sync(uint32_t pair) {
   asm volatile("bar.sync %0, 256;" ::"r"(pair + 1u) : "memory");
 }
 
-// Issue tile t's MMAs for the (A plane, B plane, accumulator column) products of `Prod` and commit them to
-// the tile's mbarrier.  Called by one thread.
+// Issue tile t's MMAs and commit them to the tile's mbarrier.  Called by one thread.
+// complex64: the six products x_i w_j with i + j <= 2 (i: A plane, j: B plane) into one 32-column accumulator.
+// complex128: the products t_a u_b accumulate per digit level L = a + b = 4..10 in columns 32 (L - 4) .. + 31.
+// The B planes sit in shared memory as [0, u_0, u_1, .., u_5] (a zero plane first, each plane 32 rows of N),
+// and consecutive planes continue the 8-row-group stride, so for one A plane a the window of planes
+// u_{4-a} .. u_{10-a} is a single B operand of N = 32 (levels) rows: one MMA computes t_a's products for
+// every level at once.  a = 5 goes first over all seven levels (its window starts at the zero plane: level 4
+// gets t_5 * 0) and initialises the accumulator; a = 4 .. 0 then add levels 4 .. a + 5 (N = 32 (a + 2)).  That
+// is 6 MMAs per K step instead of one per digit pair (26), for the same products.
 template <int MODE>
 __device__ __forceinline__ void tc_issue(const TcCtx &tc, uint32_t t, uint32_t R, const unsigned char *myB) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -411,7 +423,6 @@ __device__ __forceinline__ void tc_issue(const TcCtx &tc, uint32_t t, uint32_t R
   if constexpr (MODE == MODE_C64_F32) {
     const uint32_t d = tc.tmem + t * kBlockK;
     uint32_t acc = 0;
-    // products x_i w_j with i + j <= 2 (i: A plane, j: B plane), one accumulator
 #pragma unroll
     for (int pr = 0; pr < 6; ++pr) {
       const int i = pr == 2 || pr == 4 ? 1 : pr == 5 ? 2 : 0;
@@ -419,25 +430,23 @@ __device__ __forceinline__ void tc_issue(const TcCtx &tc, uint32_t t, uint32_t R
 #pragma unroll
       for (int ks = 0; ks < kBlockK / 16; ++ks) {
         tc_mma(d, tc_desc(a0 + (uint32_t)i * R * kTcRowBytes + (uint32_t)ks * 256),
-               tc_desc(bb0 + (uint32_t)j * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), acc);
+               tc_desc(bb0 + (uint32_t)j * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), tc_idesc(kBlockK), acc);
         acc = 1;
       }
     }
   } else {
-    // digit products t_a u_b with a + b = L accumulated per level L = 4..10
-#pragma unroll 1
-    for (int L = 4; L <= 10; ++L) {
-      const uint32_t d = tc.tmem + t * (7 * kBlockK) + (uint32_t)(L - 4) * kBlockK;
-      uint32_t acc = 0;
-      const int alo = L > 5 ? L - 5 : 0, ahi = L < 5 ? L : 5;
-#pragma unroll 1
-      for (int a = alo; a <= ahi; ++a) {
+    const uint32_t d = tc.tmem + t * (7 * kBlockK);
+    uint32_t acc = 0;
 #pragma unroll
-        for (int ks = 0; ks < kBlockK / 16; ++ks) {
-          tc_mma(d, tc_desc(a0 + (uint32_t)a * R * kTcRowBytes + (uint32_t)ks * 256),
-                 tc_desc(bb0 + (uint32_t)(L - a) * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), acc);
-          acc = 1;
-        }
+    for (int a = kBlockDigitsC128 - 1; a >= 0; --a) {
+      // window start: plane u_{4 - a} (index 5 - a in the array), the zero plane (index 0) for a = 5
+      const uint32_t first = a == kBlockDigitsC128 - 1 ? 0u : (uint32_t)(5 - a);
+      const uint32_t n = a == kBlockDigitsC128 - 1 ? 7u * kBlockK : (uint32_t)(a + 2) * kBlockK;
+#pragma unroll
+      for (int ks = 0; ks < kBlockK / 16; ++ks) {
+        tc_mma(d, tc_desc(a0 + (uint32_t)a * R * kTcRowBytes + (uint32_t)ks * 256),
+               tc_desc(bb0 + first * (uint32_t)kBlockPlaneBytes + (uint32_t)ks * 256), tc_idesc(n), acc);
+        acc = 1;
       }
     }
   }
@@ -568,11 +577,11 @@ __device__ __forceinline__ void tc_load_levels(uint32_t a, float (&d)[7][4]) {
     for (int e = 0; e < 4; ++e) d[L][e] = __uint_as_float(r[4 * L + e]);
 }
 
-// y = 2^(E - 62) S with S = sum_{i=0..6} D_i 256^i (D_i: digit level 4 + i, exact integers below 2^22), as a
-// normalised double-float.  S is formed exactly in 64-bit integer arithmetic (each D_i enters as the bit
-// pattern of D_i + 1.5 * 2^23, the pattern's constant part removed once at the end; all sums wrap modulo
-// 2^64, and S itself fits), then split into 22-bit pieces that convert to float exactly.
-__device__ __forceinline__ dfv levels_to_df(const float (&d)[7], float isc) {
+// S = sum_{i=0..6} D_i 256^i (D_i: digit level 4 + i, exact integers below 2^22) modulo 2^64, formed exactly
+// in 64-bit integer arithmetic: each D_i enters as the bit pattern of D_i + 1.5 * 2^23, the patterns' constant
+// part removed once at the end (all sums wrap modulo 2^64; S itself is below 2^62 in magnitude).  The block's
+// output is y = 2^(E - 62) S.
+__device__ __forceinline__ uint64_t levels_to_int(const float (&d)[7]) {
   uint32_t b[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) b[i] = __float_as_uint(__fadd_rn(d[i], 12582912.0f));
@@ -580,8 +589,12 @@ __device__ __forceinline__ dfv levels_to_df(const float (&d)[7], float isc) {
   constexpr uint64_t kBias = kMagic * (1ull + (1ull << 8) + (1ull << 16) + (1ull << 24) + (1ull << 32) + (1ull << 40) +
                                        (1ull << 48));
   const uint32_t top = b[4] + (b[5] << 8) + (b[6] << 16);
-  const uint64_t acc = (uint64_t)b[0] + ((uint64_t)b[1] << 8) + ((uint64_t)b[2] << 16) + ((uint64_t)b[3] << 24) +
-                       ((uint64_t)top << 32) - kBias;
+  return (uint64_t)b[0] + ((uint64_t)b[1] << 8) + ((uint64_t)b[2] << 16) + ((uint64_t)b[3] << 24) +
+         ((uint64_t)top << 32) - kBias;
+}
+
+// y = 2^(E - 62) S as a normalised double-float: S split into 22-bit pieces that convert to float exactly.
+__device__ __forceinline__ dfv int_to_df(uint64_t acc, float isc) {
   const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
   const uint32_t c0 = lo & 0x3FFFFFu, c1 = __funnelshift_r(lo, hi, 22) & 0x3FFFFFu;
   const int32_t c2 = (int32_t)hi >> 12;
@@ -592,6 +605,50 @@ __device__ __forceinline__ dfv levels_to_df(const float (&d)[7], float isc) {
   two_sum(__fmul_rn(f2, 0x1p44f), __fmul_rn(f1, 0x1p22f), h, e);
   const dfv r = fast_two_sum(h, __fadd_rn(e, f0));
   return dfv{__fmul_rn(r.h, isc), __fmul_rn(r.l, isc)};
+}
+
+// Fixed-point hand-off between two blocks.  When the next gate record of the pass is also a block, a block
+// writes each output component as w = v + kDigitBias in its 8-byte half of the slot, with v = round(S / 2^15)
+// = round(y 2^(47 - E)): the very integer the next block's digit split would round y to (the chunk's E is the
+// same for both).  With kDigitBias = 128 (1 + 256 + .. + 256^5), bytes 0..4 of w are t_0 + 128 .. t_4 + 128
+// and w >> 40 = t_5 + 128 for balanced digits t_a of v (t_5 in [-128, 128]: |v| <= 2^47 keeps w in
+// [0, 2^48 + 2^40)), so the next block reads its six digits with one byte select and one exact float
+// subtraction each, and skips both the double-float conversion and the digit split.
+constexpr uint64_t kDigitBias = 0x808080808080ull;
+
+__device__ __forceinline__ uint2 int_to_fixed(uint64_t acc) {
+  const uint64_t w = (uint64_t)(((int64_t)acc + (1ll << 14)) >> 15) + kDigitBias;
+  return make_uint2((uint32_t)w, (uint32_t)(w >> 32));
+}
+
+// The float 2^23 + b for a byte b selected from x (0x4B0000bb), minus 2^23 + 128: b - 128 exactly.
+__device__ __forceinline__ float byte_digit(uint32_t x, uint32_t sel) {
+  return __fadd_rn(__uint_as_float(__byte_perm(x, 0x4B000000u, sel)), -8388736.0f);
+}
+
+__device__ __forceinline__ void fixed_digits(uint2 w, float (&t)[6]) {
+  t[0] = byte_digit(w.x, 0x7650u);
+  t[1] = byte_digit(w.x, 0x7651u);
+  t[2] = byte_digit(w.x, 0x7652u);
+  t[3] = byte_digit(w.x, 0x7653u);
+  t[4] = byte_digit(w.y, 0x7650u);
+  t[5] = __fadd_rn(__uint_as_float(0x4B000000u | (w.y >> 8)), -8388736.0f);
+}
+
+// A planes of part h of row r from the previous block's fixed-point output.
+__device__ __forceinline__ void tc_rows_c128_fixed(const float4 *sm, uint32_t b0, const int (&pb)[kBlockBits],
+                                                   uint32_t h, unsigned char *row, uint32_t R) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float dg[8][6];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      fixed_digits(reinterpret_cast<const uint2 *>(&sm[b0 ^ tc_elem<MODE_C128_DF32>(q * 8 + e, pb)])[h], dg[e]);
+#pragma unroll
+    for (int a = 0; a < kBlockDigitsC128; ++a)
+      st_planes(row + (size_t)a * R * kTcRowBytes + h * 256 + q * 128, bf2_pack(dg[0][a], dg[1][a]),
+                bf2_pack(dg[2][a], dg[3][a]), bf2_pack(dg[4][a], dg[5][a]), bf2_pack(dg[6][a], dg[7][a]));
+  }
 }
 
 // Chunk exponent of a complex128 chunk in working form: E with 2^E above the chunk's 2-norm (from the high
@@ -627,24 +684,26 @@ __device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, 
 // CTA synchronises only at the end of the block (the next block's rows mix amplitudes of every tile).
 template <int MODE>
 __device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr, typename Arith<MODE>::S *sm, int k,
-                                         TcCtx &tc) {
+                                         TcCtx &tc, bool next_block, uint32_t sx) {
   constexpr int planes = MODE == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128;
   const uint32_t tid = threadIdx.x, g = tid >> 7, pair = g >> 1, h = g & 1u, lane = tid & 127u;
   const uint32_t R = 1u << (k - kBlockBits), ntiles = R / 128;
   const unsigned char *src = reinterpret_cast<const unsigned char *>(ghdr) + hdr.gmask;  // offset from the blob record
-  unsigned char *myB = tc.opB + (size_t)pair * planes * kBlockPlaneBytes;
+  unsigned char *myB = tc.opB + (size_t)pair * tc_bplanes<MODE>() * kBlockPlaneBytes;
+  unsigned char *myBd = myB + (MODE == MODE_C64_F32 ? 0 : kBlockPlaneBytes);  // the block's planes
   int pb[kBlockBits];
 #pragma unroll
   for (int j = 0; j < kBlockBits; ++j) pb[j] = (int)((hdr.cmask >> (8 * j)) & 0xffu);
   int ok = tc.ok;
   if (pair < ntiles) {
     for (uint32_t u = tid & 255u; u < (uint32_t)(planes * kBlockPlaneBytes / 16); u += 256)
-      cp_async16(myB + 16u * u, src + 16u * u);
+      cp_async16(myBd + 16u * u, src + 16u * u);
     for (uint32_t t = pair; t < ntiles; t += kTcPairs) {
       const uint32_t r = t * 128 + lane;
-      const uint32_t b0 = tc_row_base<MODE>(r, pb);
+      const uint32_t b0 = tc_row_base<MODE>(r, pb) ^ sx;
       unsigned char *row = tc.opA + (r / 8) * 512 + (r % 8) * 16;
       if constexpr (MODE == MODE_C64_F32) tc_rows_c64(sm, b0, pb, h, row, R);
+      else if (tc.fixed_in) tc_rows_c128_fixed(sm, b0, pb, h, row, R);
       else tc_rows_c128(sm, b0, pb, h, row, R, tc.sc);
       if (t == pair) cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -654,7 +713,7 @@ __device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr
     for (uint32_t t = pair; t < ntiles; t += kTcPairs) {
       if (ok) ok = tc_wait(tc.mbar + t, tc.phase) ? 1 : 0;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t b0 = tc_row_base<MODE>(t * 128 + lane, pb);
+      const uint32_t b0 = tc_row_base<MODE>(t * 128 + lane, pb) ^ sx;
       const uint32_t tl = tc.tmem + ((tid & 96u) << 16);
       if constexpr (MODE == MODE_C64_F32) {
         float dv[16];
@@ -677,9 +736,14 @@ __device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr
               float lv[7];
 #pragma unroll
               for (int L = 0; L < 7; ++L) lv[L] = d[L][e];
-              const dfv y = levels_to_df(lv, tc.isc);
+              const uint64_t acc = levels_to_int(lv);
               const uint32_t o = b0 ^ hiofs ^ tc_elem<MODE_C128_DF32>(e, pb);
-              reinterpret_cast<float2 *>(&sm[o])[h] = make_float2(y.h, y.l);
+              if (next_block) {
+                reinterpret_cast<uint2 *>(&sm[o])[h] = int_to_fixed(acc);
+              } else {
+                const dfv y = int_to_df(acc, tc.isc);
+                reinterpret_cast<float2 *>(&sm[o])[h] = make_float2(y.h, y.l);
+              }
             }
           }
         }
@@ -691,6 +755,27 @@ __device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr
   if (tc.ok) tc.phase ^= 1u;
   if (!ok && tc.ok && tid == 0) atomicOr(tc.err, 1u);
   tc.ok = ok;
+  if constexpr (MODE == MODE_C128_DF32) tc.fixed_in = next_block ? 1 : 0;
+}
+
+// An exchange of a chunk bit with no control inside the chunk (its controls outside, if any, are tested per
+// chunk before): a pure relabelling of the chunk's slots.
+__device__ __forceinline__ bool lazy_x(const DevGate &g) {
+  return g.cls == GC_X && g.target >= 0 && (uint32_t)g.cmask == 0u;
+}
+
+// Apply pending exchanges xm to the chunk's data: slots j and j ^ xm trade places.  Ends with a barrier.
+template <int MODE, int NT>
+__device__ __forceinline__ void apply_exchanges(typename Arith<MODE>::S *sm, uint32_t nloc, uint32_t xm) {
+  for (uint32_t o = threadIdx.x; o < nloc; o += NT) {
+    const uint32_t j = o ^ xm;
+    if (o < j) {
+      const typename Arith<MODE>::S a = sm[slot<MODE>(o)], b = sm[slot<MODE>(j)];
+      sm[slot<MODE>(o)] = b;
+      sm[slot<MODE>(j)] = a;
+    }
+  }
+  __syncthreads();
 }
 
 // Shared-memory layout: 2^k working amplitudes, then 2^(k-c) row offsets (uint64), then 32 words for the
@@ -754,16 +839,40 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     }
   }
   __syncthreads();
-  if constexpr (TC && MODE == MODE_C128_DF32) tc_chunk_scale(sm, nloc, *tc);
+  if constexpr (TC && MODE == MODE_C128_DF32) {
+    tc_chunk_scale(sm, nloc, *tc);
+    tc->fixed_in = 0;
+  }
 
+  // Tensor-core passes apply an exchange (X) with no control inside the chunk lazily: the pending exchanges
+  // form a mask xm, amplitude j of the chunk sits in slot slot(j ^ xm) (slot is linear over GF(2)), blocks read
+  // and write through that map, and the mask is applied to the data only before a per-gate record or folded
+  // into the final store.
+  uint32_t xm = 0;
   for (int gi = 0; gi < p.ngates; ++gi) {
     const DevGate &g = GR[gi];
     if (g.cls == GC_BLOCK) {  // its gmask is the offset of its operand planes, not a control mask
-      if constexpr (TC) tc_block<MODE>(g, p.gates + gi, sm, k, *tc);
+      if constexpr (TC) {
+        // a block followed by another block (lazy exchanges between them aside) hands its output over in
+        // fixed point (complex128)
+        int nx = gi + 1;
+        while (nx < p.ngates && lazy_x(GR[nx])) ++nx;
+        tc_block<MODE>(g, p.gates + gi, sm, k, *tc, nx < p.ngates && GR[nx].cls == GC_BLOCK, slot<MODE>(xm));
+      }
       continue;
     }
     const uint64_t gmask = g.gmask;
     if ((base & gmask) != gmask) continue;  // a control bit outside the chunk is 0: the gate skips this chunk
+    if constexpr (TC) {
+      if (lazy_x(g)) {
+        xm ^= 1u << g.target;
+        continue;
+      }
+      if (xm != 0u) {
+        apply_exchanges<MODE, NT>(sm, nloc, xm);
+        xm = 0u;
+      }
+    }
     const uint32_t cls = g.cls;
     if (cls == GC_ROW) continue;  // consumed with its GC_DENSE4 record
     if (cls == GC_DENSE4) {
@@ -823,9 +932,10 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     __syncthreads();
   }
 
+  const uint32_t sx = slot<MODE>(xm);  // 0 unless lazy exchanges are pending (tensor-core passes)
   if (!p.permuted) {
     for (uint32_t o = tid; o < nloc; o += NT)
-      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(o)]);
+      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(o) ^ sx]);
   } else {
     // Store with chunk-local bit j sent to physical bit qpos_out[j]: output slot o (bits in the ascending
     // order of Q) takes local amplitude P(o), bit j of P(o) = bit src_bit[j] of o.
@@ -833,7 +943,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     for (int j = 0; j < k; ++j) plo |= (((tid & 255u) >> p.src_bit[j]) & 1u) << j;  // P(o mod 256), NT % 256 == 0
     const uint32_t *ptab = (const uint32_t *)(rowoff + nrows);
     for (uint32_t o = tid; o < nloc; o += NT)
-      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(plo | ptab[o >> 8])]);
+      psi[base + rowoff[o >> c] + (o & lowmask)] = M::store(sm[slot<MODE>(plo | ptab[o >> 8]) ^ sx]);
   }
   __syncthreads();
 }
@@ -861,7 +971,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, ui
   TcCtx tc;
   tc.opA = smraw + tc_smem_base<MODE>(p.k);
   tc.opB = tc.opA + (size_t)tc_planes<MODE>() * R * kTcRowBytes;
-  tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)kTcPairs * tc_planes<MODE>() * kBlockPlaneBytes);
+  tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)kTcPairs * tc_bplanes<MODE>() * kBlockPlaneBytes);
+  if constexpr (MODE != MODE_C64_F32) {
+    // the zero plane in front of each pair's digit planes (never written again)
+    for (uint32_t u = threadIdx.x; u < (uint32_t)(kTcPairs * kBlockPlaneBytes / 16); u += kTcThreads) {
+      const uint32_t pr = u / (kBlockPlaneBytes / 16), w = u % (kBlockPlaneBytes / 16);
+      reinterpret_cast<uint4 *>(tc.opB + (size_t)pr * tc_bplanes<MODE>() * kBlockPlaneBytes)[w] = make_uint4(0, 0, 0, 0);
+    }
+  }
   uint32_t *tslot = reinterpret_cast<uint32_t *>(tc.mbar + kTcMaxTiles);
   tc.red = reinterpret_cast<float *>(tc.mbar + kTcMaxTiles + 1);
   if (threadIdx.x < 32) {
@@ -880,6 +997,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, ui
   tc.phase = 0;
   tc.ok = 1;
   tc.err = err;
+  tc.fixed_in = 0;
   // The pass's gate records, copied once to shared memory (every chunk reads each of them); a pass with more
   // than kTcGateCopy records reads them from global memory.
   DevGate *gcopy = nullptr;

@@ -161,13 +161,24 @@ __global__ void k_probs(const G *__restrict__ psi, int n, const Perm pm, uint64_
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Norm (the normalisation condition of Sec. II.A): each thread accumulates |alpha|^2 of its amplitudes in
-// native FP64 (two fused multiply-adds per amplitude on the exact double value of each component), the block
-// adds the per-thread values in FP64 in a fixed tree order, and a second kernel adds the per-block partials in
-// index order: the result does not depend on timing.
+// Norm (the normalisation condition of Sec. II.A).  Each thread keeps an FP64 accumulator; the block adds the
+// per-thread values in FP64 in a fixed tree order, and a second kernel adds the per-block partials with
+// compensation in a fixed order, so the result does not depend on timing.  Every thread has kNormLoads 16-byte loads in flight per
+// iteration (HBM latency needs that many bytes in flight per SM).
+// * complex128: every component's square is added by one FP64 fused multiply-add on its exact value.
+// * complex64: a float's square is exact as a pair p + e (one multiply, one FMA); the 16 squares of the
+//   iteration's eight amplitudes are summed with error-free TwoSums into s, their errors and the e's summed
+//   the same way into c, and only the errors of that second sum are rounded, into d (cascaded compensated
+//   summation in the manner of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005: s + c + d is the
+//   group's sum to about 2^-70 of it).  s, c and d, each converted exactly to double, enter the FP64
+//   accumulator: three FP64 additions per eight amplitudes on GB300's slow FP64 pipe instead of two per
+//   amplitude, and an error below that of one FP64 addition per group.  (Summing the small terms in a single
+//   FP32 sum instead leaves a bias of about 2^-49 of each group's sum.)
+// A sign (-1)^popcount(k & pmask) is applied by flipping one factor's sign bit (exact).
 // ------------------------------------------------------------------------------------------------------
 constexpr int kNormThreads = 256;
 constexpr int kNormBlocksPerSm = 4;
+constexpr int kNormLoads = 4;
 
 // The exact double value of a float, with integer operations (the float -> double conversion instruction runs
 // on GB300's slow FP64/conversion unit).  Normal floats: sign, exponent re-biased by 1023 - 127, mantissa
@@ -184,14 +195,68 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double flip_if(double x, bool neg) {
   return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
 }
+__device__ __forceinline__ float flipf_if(float x, bool neg) {
+  return neg ? __uint_as_float(__float_as_uint(x) ^ 0x80000000u) : x;
+}
 
-// Stage 1 of sum_k (-1)^popcount(k & pmask) |psi_k|^2 over physical indices k (pmask = 0: the norm).  The sign
-// is applied by flipping one factor's sign bit (exact), so each term is one FP64 multiply-add.
+// s + c + d += (+/-) x^2 (see above): x^2 = p + e exactly, s + r = s + p exactly, r + e = q + t exactly,
+// c + q = c' + u exactly; only the small terms t + u (each below 2^-48 of the running sum) are rounded, into d.
+__device__ __forceinline__ void sq_add(float x, bool neg, float &s, float &c, float &d) {
+  const float xs = flipf_if(x, neg);
+  const float p = __fmul_rn(xs, x);
+  const float e = __fmaf_rn(xs, x, -p);
+  float t1, r, q, t, u;
+  two_sum(s, p, t1, r);
+  s = t1;
+  two_sum(r, e, q, t);
+  two_sum(c, q, t1, u);
+  c = t1;
+  d = __fadd_rn(d, __fadd_rn(t, u));
+}
+
+// Stage 1 of sum_k (-1)^popcount(k & pmask) |psi_k|^2 over physical indices k (pmask = 0: the norm).
 template <typename G, bool IS_DOUBLE>
 __global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ psi, uint64_t N, uint64_t pmask,
                                                         double *__restrict__ partials) {
+  constexpr uint64_t kPer = IS_DOUBLE ? 1 : 2;  // amplitudes per 16-byte load
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t NV = N / kPer;                  // 16-byte units
   double acc = 0.0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+  // main loop: kNormLoads units per thread per iteration, units tid + j * nthreads of the iteration's span
+  const uint64_t span = nthreads * kNormLoads, full = NV / span * span;
+  for (uint64_t base = 0; base < full; base += span) {
+    if constexpr (IS_DOUBLE) {
+      double2 v[kNormLoads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) v[j] = psi[base + tid + (uint64_t)j * nthreads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) {
+        const bool neg = (__popcll((base + tid + (uint64_t)j * nthreads) & pmask) & 1) != 0;
+        acc = __fma_rn(flip_if(v[j].x, neg), v[j].x, acc);
+        acc = __fma_rn(flip_if(v[j].y, neg), v[j].y, acc);
+      }
+    } else {
+      const float4 *p4 = reinterpret_cast<const float4 *>(psi);
+      float4 v[kNormLoads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) v[j] = p4[base + tid + (uint64_t)j * nthreads];
+      float s = 0.0f, c = 0.0f, d = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) {
+        const uint64_t k0 = 2 * (base + tid + (uint64_t)j * nthreads);
+        const bool n0 = (__popcll(k0 & pmask) & 1) != 0, n1 = (__popcll((k0 + 1) & pmask) & 1) != 0;
+        sq_add(v[j].x, n0, s, c, d);
+        sq_add(v[j].y, n0, s, c, d);
+        sq_add(v[j].z, n1, s, c, d);
+        sq_add(v[j].w, n1, s, c, d);
+      }
+      // s + (c + d), with c + d formed first (both far below s)
+      acc = __dadd_rn(acc, __dadd_rn(f2d_exact(s), __dadd_rn(f2d_exact(c), f2d_exact(d))));
+    }
+  }
+  // the rest, one amplitude at a time (all of it when N < 2 span)
+  for (uint64_t i = full * kPer + tid; i < N; i += nthreads) {
     const G v = psi[i];
     const bool neg = (__popcll(i & pmask) & 1) != 0;
     double x, y;
@@ -215,21 +280,82 @@ __global__ void __launch_bounds__(kNormThreads) k_norm1(const G *__restrict__ ps
   if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
-__global__ void k_norm2(const double *__restrict__ partials, int nparts, double *__restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += partials[i];
-    out[0] = s;
-  }
+// Error-free sum of two doubles (Knuth's TwoSum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
-template <typename G>
+// Stage 2: the per-block partials added with compensation by one warp (lane l takes partials l, l + 32, ..
+// in index order, keeping the rounding errors of its TwoSums in c; the 32 (s, c) pairs are then combined by a
+// fixed butterfly of TwoSums), so the result is the correctly rounded sum of the partials up to a few units in
+// the last place, in a fixed order.
+__global__ void k_norm2(const double *__restrict__ partials, int nparts, double *__restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double s = 0.0, c = 0.0, e;
+  for (int i = threadIdx.x; i < nparts; i += 32) {
+    two_sum_d(s, partials[i], s, e);
+    c = __dadd_rn(c, e);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double so = __shfl_xor_sync(0xffffffffu, s, off), co = __shfl_xor_sync(0xffffffffu, c, off);
+    // the lower lane's pair first, so both lanes form the same sum
+    const bool low = (threadIdx.x & off) == 0;
+    two_sum_d(low ? s : so, low ? so : s, s, e);
+    c = __dadd_rn(__dadd_rn(low ? c : co, low ? co : c), e);
+  }
+  if (threadIdx.x == 0) out[0] = __dadd_rn(s, c);
+}
+
+// psi *= 1 / sqrt(norm2), the factor f formed in FP64 once per thread.  complex128: one FP64 multiply per
+// component.  complex64: f = fh + fl (two floats, fl = f - fh exactly rounded) and x f = fma(x, fh, x fl) in
+// FP32, within an ulp of the correctly rounded product, without the FP64 pipe.  kNormLoads 16-byte units per
+// thread per iteration, as in the norm.
+template <typename G, bool IS_DOUBLE>
 __global__ void k_scale(G *__restrict__ psi, uint64_t N, const double *__restrict__ norm2) {
   const double f = 1.0 / sqrt(norm2[0]);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+  const float fh = (float)f, fl = (float)(f - (double)fh);
+  constexpr uint64_t kPer = IS_DOUBLE ? 1 : 2;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t NV = N / kPer, span = nthreads * kNormLoads, full = NV / span * span;
+  for (uint64_t base = 0; base < full; base += span) {
+    if constexpr (IS_DOUBLE) {
+      double2 v[kNormLoads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) v[j] = psi[base + tid + (uint64_t)j * nthreads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) {
+        v[j].x *= f;
+        v[j].y *= f;
+        psi[base + tid + (uint64_t)j * nthreads] = v[j];
+      }
+    } else {
+      float4 *p4 = reinterpret_cast<float4 *>(psi);
+      float4 v[kNormLoads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) v[j] = p4[base + tid + (uint64_t)j * nthreads];
+#pragma unroll
+      for (int j = 0; j < kNormLoads; ++j) {
+        v[j].x = __fmaf_rn(v[j].x, fh, __fmul_rn(v[j].x, fl));
+        v[j].y = __fmaf_rn(v[j].y, fh, __fmul_rn(v[j].y, fl));
+        v[j].z = __fmaf_rn(v[j].z, fh, __fmul_rn(v[j].z, fl));
+        v[j].w = __fmaf_rn(v[j].w, fh, __fmul_rn(v[j].w, fl));
+        p4[base + tid + (uint64_t)j * nthreads] = v[j];
+      }
+    }
+  }
+  for (uint64_t i = full * kPer + tid; i < N; i += nthreads) {
     G v = psi[i];
-    v.x = (decltype(v.x))((double)v.x * f);
-    v.y = (decltype(v.y))((double)v.y * f);
+    if constexpr (IS_DOUBLE) {
+      v.x *= f;
+      v.y *= f;
+    } else {
+      v.x = __fmaf_rn(v.x, fh, __fmul_rn(v.x, fl));
+      v.y = __fmaf_rn(v.y, fh, __fmul_rn(v.y, fl));
+    }
     psi[i] = v;
   }
 }
@@ -464,8 +590,8 @@ cudaError_t launch_sample_block(const void *psi, int n, int mode, const int *per
 cudaError_t launch_scale(void *psi, int n, int mode, const double *d_norm2, cudaStream_t st) {
   const uint64_t N = 1ull << n;
   const unsigned grid = grid_for(N, 256);
-  if (mode == MODE_C64_F32) k_scale<float2><<<grid, 256, 0, st>>>((float2 *)psi, N, d_norm2);
-  else k_scale<double2><<<grid, 256, 0, st>>>((double2 *)psi, N, d_norm2);
+  if (mode == MODE_C64_F32) k_scale<float2, false><<<grid, 256, 0, st>>>((float2 *)psi, N, d_norm2);
+  else k_scale<double2, true><<<grid, 256, 0, st>>>((double2 *)psi, N, d_norm2);
   return cudaGetLastError();
 }
 

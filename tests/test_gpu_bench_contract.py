@@ -44,6 +44,8 @@ def test_bench_line_has_the_contract_keys():
     acc = d["accuracy"]
     assert acc["n"] == 16 and acc["c128_df32"]["max_abs_err"] < 1e-12 and acc["c128_f64"]["max_abs_err"] < 1e-12
     assert acc["c64"]["one_minus_fidelity"] < 1e-8
+    q = d["qft"]["qft20"]
+    assert q["n"] == 20 and q["value"] > 0 and q["steps"] == 5 and q["warmup"] == 3
 
 
 def test_reference_arm_line():

@@ -239,6 +239,54 @@ def test_norm_probabilities_and_readout(mode):
         B.sv_destroy(h)
 
 
+def fsum_signed(v, mask):
+    """sum_k (-1)^popcount(k & mask) |v_k|^2 with the squares in FP64, added with math.fsum."""
+    import math
+    k = np.arange(v.size, dtype=np.uint64)
+    par = np.zeros(v.size, dtype=np.int64)
+    m = k & np.uint64(mask)
+    while np.any(m):
+        par ^= (m & np.uint64(1)).astype(np.int64)
+        m >>= np.uint64(1)
+    sg = 1.0 - 2.0 * par
+    return math.fsum(np.concatenate([sg * v.real * v.real, sg * v.imag * v.imag]).tolist())
+
+
+@pytest.mark.parametrize("dtype", [B.SV_C128, B.SV_C64], ids=["c128", "c64"])
+@pytest.mark.parametrize("n", [21, 22])
+def test_norm_expectation_and_renormalisation_past_the_vector_span(dtype, n):
+    """From n = 21 on most of the reduction runs in the norm kernel's vector loop (four 16-byte loads per thread
+    and iteration) and the rest in its tail: the FP64 norm and Pauli-Z expectations against the correctly
+    rounded sums of the GPU's own amplitudes, and the renormalised amplitudes against an FP64 rescale of the
+    amplitudes read before it (a state written with norm 1.7^2, so the factor is far from 1)."""
+    rng = np.random.default_rng(40 + n)
+    v = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    v *= 1.7 / np.linalg.norm(v)
+    h = B.sv_create(n, dtype)
+    try:
+        B.sv_write_amplitudes(h, 0, v.astype(np.complex128 if dtype == B.SV_C128 else np.complex64))
+        mine = B.sv_read_amplitudes(h).astype(np.complex128)
+        nrm = B.sv_norm(h)
+        assert abs(nrm - fsum_norm2(mine)) <= 1e-15 * nrm
+        for mask in (1, (1 << (n - 1)) | 6, (1 << n) - 1):
+            ez = B.sv_expect_z(h, mask)
+            assert abs(ez - fsum_signed(mine, mask)) <= 1e-15 * nrm, mask
+        B.sv_renormalize(h)
+        after = B.sv_read_amplitudes(h).astype(np.complex128)
+        want = mine / np.sqrt(nrm)
+        if dtype == B.SV_C128:
+            np.testing.assert_allclose(after, want, rtol=2 ** -50, atol=0)
+            assert abs(B.sv_norm(h) - 1.0) < 1e-14
+        else:
+            # within one float ulp of the FP64 rescale, componentwise
+            for got, ref in ((after.real, want.real), (after.imag, want.imag)):
+                ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+                assert np.all(np.abs(got - ref) <= ulp)
+            assert abs(B.sv_norm(h) - 1.0) < 1e-6
+    finally:
+        B.sv_destroy(h)
+
+
 def test_buffer_state_over_torch_tensor_stays_in_logical_order():
     torch = pytest.importorskip("torch")
     n = 15
