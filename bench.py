@@ -169,10 +169,12 @@ class OracleRunner:
 RENORM_PERIOD = 64
 
 
-def gpu_results_for_accuracy(B, n_acc, depth):
+def gpu_results_for_accuracy(B, n_acc, depth, opts=None):
     """The GPU's final states for the bench's circuit family at a size the host oracle finishes in seconds:
     complex128 double-float (with the FP64 share), all-FP64, and complex64 without and with periodic
-    renormalisation (every RENORM_PERIOD gates, FP64 norm).  Compared in the CPU leg."""
+    renormalisation (every RENORM_PERIOD gates, FP64 norm).  `opts` maps a dtype to the options of the timed
+    run ({option: value}: chunk size, FP64 share, tensor blocks), applied to the double-float and complex64
+    states so that their errors are those of the configuration timed.  Compared in the CPU leg."""
     w = C.random_workload(n_acc, depth, seed=SEED)
     res = {}
     for name, dt, arith, renorm in (("c128_df32", B.SV_C128, B.SV_ARITH_DF32, 0),
@@ -183,6 +185,9 @@ def gpu_results_for_accuracy(B, n_acc, depth):
         try:
             if dt == B.SV_C128:
                 B.sv_set_option(h, B.SV_OPT_ARITH, arith)
+            if arith != B.SV_ARITH_F64:
+                for opt, val in (opts or {}).get(dt, {}).items():
+                    B.sv_set_option(h, opt, val)
             B.sv_set_option(h, B.SV_OPT_RENORM_PERIOD, renorm)
             B.sv_apply_circuit(h, w.gates)
             res[name] = B.sv_read_amplitudes(h).astype(np.complex128)
@@ -457,6 +462,7 @@ def run_ours(args):
     f64_peak = 152 * 1.73 * sm_hz * 1e6 / 1e12  # measured FP64 multiply-adds per clock per SM
     f64_achieved = f64_fma_launch / (avg_ms * 1e-3) / 1e12 if c128["fused_launches"] else None
     traffic = committed_traffic(args.n, "k_fused_tc" if c128["stats"]["blocks"] else "k_fused_mixed")
+    blocks_on = c128["stats"]["blocks"] > 0
     # init, passes, sweeps, bit-permutation passes, the two norm kernels, and the two product-start kernels
     folded_start = c128["stats"]["absorbed"] > 0
     launches_per_step = (1 + c128["stats"]["passes"] + c128["stats"]["sweep_gates"] + c128["stats"]["remaps"] + 2
@@ -472,20 +478,29 @@ def run_ours(args):
             ks, picked = batch_chunk_sizes(B, [w.n for w in ws_b], dt_b, not args.no_autotune)
             batched[name] = {**batched_measure(B, ws_b, dt_b, ks), "chunk_qubits": picked or "default"}
         batched["workload"] = "512 random circuits, n log-uniform in [10, 22], 10-40 layers, seed 1004"
-        qft = {"qft20": qft_measure(B, "qft20", 5, 3)}
+        qft = {"qft20": qft_measure(B, "qft20", 5, 3, tensor_blocks.get(B.SV_C128, 0))}
         if args.n == N_QUBITS and not args.no_n33:
             import torch
             free_b, _ = torch.cuda.mem_get_info()
             if free_b >= (16 << 33) + (2 << 30):
-                qft["qft33"] = qft_measure(B, "qft33", 1, 1)
+                qft["qft33"] = qft_measure(B, "qft33", 1, 1, tensor_blocks.get(B.SV_C128, 0))
     # c64 with periodic renormalisation (every RENORM_PERIOD gates), one step, for its cost beside c64 without
     c64_renorm = timed(B.SV_C64, B.SV_ARITH_AUTO, 1, 1, renorm=RENORM_PERIOD)
     cpu = cpu_baseline(args.n, gates, args.cpu_seconds) if RANK == 0 and WORLD == 1 else None
     accuracy = None
     if RANK == 0:
         n_acc = min(args.n, 22)
-        w_acc, gpu_states = gpu_results_for_accuracy(B, n_acc, args.depth)
+        opts = {B.SV_C128: {B.SV_OPT_F64_SHARE: f64_share, B.SV_OPT_TENSOR_BLOCKS: tensor_blocks.get(B.SV_C128, 0)},
+                B.SV_C64: {B.SV_OPT_TENSOR_BLOCKS: tensor_blocks.get(B.SV_C64, 0)}}
+        for dt in (B.SV_C128, B.SV_C64):
+            if dt in chunk_k and chunk_k[dt] <= n_acc:
+                opts[dt][B.SV_OPT_CHUNK_QUBITS] = chunk_k[dt]
+        w_acc, gpu_states = gpu_results_for_accuracy(B, n_acc, args.depth, opts)
         accuracy = cpu_leg_accuracy(n_acc, args.depth, w_acc, gpu_states)
+        accuracy["options"] = {"c128_df32": {"f64_share": f64_share, "tensor_blocks": tensor_blocks.get(B.SV_C128, 0),
+                                             "chunk_qubits": chunk_k.get(B.SV_C128, "default")},
+                               "c64": {"tensor_blocks": tensor_blocks.get(B.SV_C64, 0),
+                                       "chunk_qubits": chunk_k.get(B.SV_C64, "default")}}
 
     if RANK != 0:
         return
@@ -538,20 +553,26 @@ def run_ours(args):
                      "frac": (hbm_achieved / peak) if hbm_achieved else None, "traffic": traffic,
                      "algorithmic_bytes_per_launch": 2 * state_bytes, "avg_launch_ms": avg_ms,
                      "launches_timed": c128["fused_launches"], "peak_source": f"{peak_kind} hbm_gbs",
-                     "limited_by": "FP32-pipe issue of the double-float arithmetic (see alu_view)",
+                     "limited_by": ("the bf16 tensor-core MMAs of the blocks' exact digit products and the digit "
+                                    "conversions around them (see tensor_core_view)" if blocks_on else
+                                    "FP32-pipe issue of the double-float arithmetic (see alu_view)"),
                      "fp64_equivalent": {"flops_per_launch": flops_launch,
                                          "achieved_tflops": (flops_launch / (avg_ms * 1e-3) / 1e12) if hbm_achieved else None,
                                          "note": "16 flops per touched amplitude of a dense gate, 6 of a diagonal one"},
-                     "alu_view": {"achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
-                                  "frac": (alu_achieved / alu_peak) if alu_achieved else None,
-                                  "algorithmic_ops_per_launch": ops_launch,
-                                  "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
-                                  "note": "operations of the double-float method itself (its chosen arithmetic)"},
+                     # the double-float method's operation count describes passes that apply every gate one by one;
+                     # with tensor-core blocks most gates never run that way, so the view is left out
+                     "alu_view": None if blocks_on else {
+                         "achieved": alu_achieved, "peak": alu_peak, "unit": "T FP32-pipe ops/s",
+                         "frac": (alu_achieved / alu_peak) if alu_achieved else None,
+                         "algorithmic_ops_per_launch": ops_launch,
+                         "peak_source": f"152 SMs x 128 lanes x {sm_hz:.0f} MHz (median SM clock sampled under load)",
+                         "note": "operations of the double-float method itself (its chosen arithmetic)"},
                      "f64_share_percent": f64_share,
                      "tensor_core_view": tensor_view(c128, args.n, chunk_k.get(B.SV_C128, 12), avg_ms, sm_hz),
-                     "fp64_pipe_view": {"achieved": f64_achieved, "peak": f64_peak, "unit": "T FP64 FMA/s",
-                                        "frac": (f64_achieved / f64_peak) if f64_achieved else None,
-                                        "peak_source": "152 SMs x 1.73 FP64 FMA/clock (probe) x median SM clock"}},
+                     "fp64_pipe_view": None if blocks_on else {
+                         "achieved": f64_achieved, "peak": f64_peak, "unit": "T FP64 FMA/s",
+                         "frac": (f64_achieved / f64_peak) if f64_achieved else None,
+                         "peak_source": "152 SMs x 1.73 FP64 FMA/clock (probe) x median SM clock"}},
         "sweep_roofline": sweeps,
         "cpu_baseline": cpu,
         "accuracy": accuracy,
@@ -570,8 +591,9 @@ def run_ours(args):
 
 def tensor_view(run, n, k, avg_ms, sm_hz):
     """bf16 tensor-core work of the dense complex128 blocks: per block and chunk of 2^k amplitudes, 2^(k-11) tiles
-    of 128 rows x 26 digit products x 2 MMAs of 128 x 32 x 16 multiply-adds.  Averaged over the fused launches of
-    the step (blocks run in some of them), against the measured bf16 dense peak scaled to the sampled clock."""
+    of 128 rows x 26 digit products of 128 x 32 x 32 multiply-adds (issued as 12 MMAs of N = 64 .. 224 per tile,
+    which also multiply one zero plane: 27/26 of this work).  Averaged over the fused launches of the step
+    (blocks run in most of them), against the measured bf16 dense peak scaled to the sampled clock."""
     blocks = run["stats"].get("blocks", 0)
     if not blocks or not run["fused_launches"]:
         return None
@@ -587,7 +609,7 @@ def tensor_view(run, n, k, avg_ms, sm_hz):
     ach = flops_launch / (avg_ms * 1e-3) / 1e12
     return {"achieved": ach, "peak": peak, "unit": "TFLOP/s (bf16 MMA)", "frac": ach / peak,
             "flops_per_launch": flops_launch, "blocks_per_step": blocks, "peak_source": src,
-            "note": "exact base-256 digit products: 26 bf16 MMA products per block row tile"}
+            "note": "exact base-256 digit products: 26 bf16 products per block and 128-row tile"}
 
 
 # FP32-pipe operations of the double-float method per amplitude (integer, float add/sub, FMA and conversion
@@ -681,14 +703,16 @@ def committed_traffic(n, kernel="k_fused_mixed"):
         return None
 
 
-def qft_measure(B, which, steps, warmup):
+def qft_measure(B, which, steps, warmup, tensor_blocks=0):
     """qft20 = QFT on n = 20 from a seeded basis state (seed 1001, 16 MiB state, L2-resident: launch overhead and
     graph replay matter); qft33 = QFT on n = 33 then 10 random layers (seed 1003, 128 GiB state).  complex128,
-    library defaults; a step = init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back."""
+    library defaults apart from SV_OPT_TENSOR_BLOCKS = `tensor_blocks`; a step = init |x>, graph replay of the
+    circuit, FP64 norm, 1024 amplitudes read back."""
     import torch
     w = C.qft_workload(20, seed=1001) if which == "qft20" else C.qft_random_workload(33, 10, seed=1003)
     h = B.sv_create(w.n, B.SV_C128)
     try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, tensor_blocks)
         def step():
             B.sv_init_basis(h, w.x0)
             B.sv_apply_circuit_graph(h, w.gates)
@@ -705,13 +729,15 @@ def qft_measure(B, which, steps, warmup):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         st = B.sv_last_plan_stats(h)
+        blk = B.sv_last_plan_blocks(h)
     finally:
         B.sv_destroy(h)
     G = len(w.gates)
     return {"metric": f"gates/s, {w.name}, complex128", "value": G / (ms / 1e3), "unit": "gates/s",
             "ms_per_step": ms, "steps": steps, "warmup": warmup, "gates": G, "n": w.n,
             "effective_hbm_gbs": G / (ms / 1e3) * 2 * (16 << w.n) / 1e9,
-            "plan": {"passes": st["passes"], "sweeps": st["sweep_gates"], "relabels": st["relabels"]},
+            "plan": {"passes": st["passes"], "sweeps": st["sweep_gates"], "relabels": st["relabels"],
+                     "tensor_blocks_option": tensor_blocks, "tensor_blocks": blk["blocks"]},
             "step": "init |x>, graph replay of the circuit, FP64 norm, 1024 amplitudes read back"}
 
 
@@ -721,7 +747,8 @@ def run_single_config(args):
     sv_build.build()
     from paper_1801_01037_gb300 import _binding as B
     B.load()
-    print(json.dumps(qft_measure(B, args.workload, args.steps, args.warmup)), flush=True)
+    tb = int(str(args.tensor_blocks).split(",")[0]) if args.tensor_blocks is not None else 0
+    print(json.dumps(qft_measure(B, args.workload, args.steps, args.warmup, tb)), flush=True)
 
 
 SIZE_CLASSES = ((0, 13), (14, 17), (18, 99))

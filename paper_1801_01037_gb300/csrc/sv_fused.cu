@@ -651,14 +651,13 @@ __device__ __forceinline__ void tc_rows_c128_fixed(const float4 *sm, uint32_t b0
   }
 }
 
-// Chunk exponent of a complex128 chunk in working form: E with 2^E above the chunk's 2-norm (from the high
-// words, with a margin of 2^-8 for the low words and rounding); sets tc.sc = 2^(47 - E), tc.isc = 2^(E - 62).
-// E is clamped to [-80, 100]: amplitudes below 2^-80 are then cut to a few 2^-127.
-__device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, TcCtx &tc) {
+// Sum of the squares of the chunk's high words (times `scale`), over the CTA; the same in every thread.
+__device__ __forceinline__ float tc_sum_squares(const float4 *sm, uint32_t nloc, float scale, TcCtx &tc) {
   float part = 0.0f;
   for (uint32_t o = threadIdx.x; o < nloc; o += kTcThreads) {
     const float4 v = sm[o];
-    part = __fmaf_rn(v.x, v.x, __fmaf_rn(v.z, v.z, part));
+    const float a = __fmul_rn(v.x, scale), b = __fmul_rn(v.z, scale);
+    part = __fmaf_rn(a, a, __fmaf_rn(b, b, part));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
@@ -667,10 +666,27 @@ __device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, 
   float tot = 0.0f;
 #pragma unroll
   for (int w = 0; w < kTcThreads / 32; ++w) tot += tc.red[w];
-  __syncthreads();  // tc.red is reused by the next chunk
+  __syncthreads();  // tc.red is reused
+  return tot;
+}
+
+// Chunk exponent of a complex128 chunk in working form: E with 2^E above the chunk's 2-norm (from the high
+// words, with a margin of 2^-8 for the low words and rounding); sets tc.sc = 2^(47 - E), tc.isc = 2^(E - 62).
+// The squares overflow FP32 once amplitudes reach 2^64: such chunks (the same decision in every thread) are
+// summed again with the values scaled by 2^-100.  E is clamped to [-80, 150]: amplitudes below 2^-80 are then
+// cut to a few 2^-127; every complex128 amplitude the library accepts (components below 2^126) leaves a chunk
+// norm below 2^150.
+__device__ __forceinline__ void tc_chunk_scale(const float4 *sm, uint32_t nloc, TcCtx &tc) {
+  float tot = tc_sum_squares(sm, nloc, 1.0f, tc);
+  int bias = 0;
+  if (!(tot <= 3.0e38f)) {
+    tot = tc_sum_squares(sm, nloc, 0x1p-100f, tc);
+    bias = 100;
+  }
   int E = 0;
   frexpf(sqrtf(__fmaf_rn(tot, 0x1p-8f, tot)) + 0x1p-126f, &E);
-  E = E < -80 ? -80 : (E > 100 ? 100 : E);
+  E += bias;
+  E = E < -80 ? -80 : (E > 150 ? 150 : E);
   tc.sc = __int_as_float((127 + 47 - E) << 23);
   const int ei = E - 62;
   tc.isc = ei >= -126 ? __int_as_float((127 + ei) << 23) : __int_as_float(1 << (ei + 149));

@@ -167,3 +167,16 @@ def test_c128_tensor_blocks_on_small_and_unnormalised_states():
         B.sv_destroy(h)
     want = run_oracle(12, g, psi0)
     assert np.max(np.abs(got - want)) <= 1e-12 * 2.0 ** -40
+    # and scaled up: a chunk norm of 2^110 (the chunk exponent must not stop below it)
+    psi1 = C.random_state(12, seed=9) * 2.0 ** 110
+    h = B.sv_create(12, B.SV_C128)
+    try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1)
+        B.sv_write_amplitudes(h, 0, psi1)
+        B.sv_apply_circuit(h, g)
+        got = B.sv_read_amplitudes(h)
+        assert B.sv_last_plan_blocks(h)["blocks"] > 0
+    finally:
+        B.sv_destroy(h)
+    want = run_oracle(12, g, psi1)
+    assert np.max(np.abs(got - want)) <= 1e-12 * 2.0 ** 110
