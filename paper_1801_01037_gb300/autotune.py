@@ -47,7 +47,11 @@ def save_cache(cache: dict) -> None:
 
 
 F64_SHARES = (0, 10, 12, 14, 16, 18, 20)
-TENSOR_BLOCKS = (0, 3, 4, 6)
+# Tensor-core block options tried per dtype.  complex64 blocks are not tried: they gain a few per cent at
+# most, and their FP32 accumulation on the tensor cores shrinks the state's norm by about 3e-7 per block (a
+# drift, not random rounding), 40x the per-gate passes' norm drift on the bench circuit; SV_OPT_TENSOR_BLOCKS
+# still turns them on by hand.
+TENSOR_BLOCKS = {B.SV_C128: (0, 3, 4, 6), B.SV_C64: (0,)}
 
 
 def time_candidate(n: int, dtype: int, arith: int, gates, k: int, repeats: int = 2, f64_share: int = -1,
@@ -97,7 +101,8 @@ def tune(n: int, dtype: int, gates, arith: int = B.SV_ARITH_AUTO, candidates=Non
         res["f64_share_ms"] = {str(s): v for s, v in sh.items()}
     if arith != B.SV_ARITH_F64:
         # dense tensor-core blocks (off, or blocks that replace at least 3, 4 or 6 dense one-qubit updates)
-        tb = {t: time_candidate(n, dtype, arith, gates, best, f64_share=share, tensor_blocks=t) for t in TENSOR_BLOCKS}
+        tb = {t: time_candidate(n, dtype, arith, gates, best, f64_share=share, tensor_blocks=t)
+              for t in TENSOR_BLOCKS[dtype]}
         res["best_tensor_blocks"] = min(tb, key=tb.get)
         res["tensor_blocks_ms"] = {str(t): v for t, v in tb.items()}
     if save:

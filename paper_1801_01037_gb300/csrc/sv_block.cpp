@@ -48,7 +48,7 @@ struct Item {
   int nrec;         // records (4 for a two-qubit gate)
   uint32_t bits;    // chunk-local bits it touches
   bool blockable;
-  double cost;      // per-gate work it saves, in dense one-qubit gate units
+  double cost;      // per-gate work it saves, in dense one-qubit gate updates of the whole chunk
 };
 
 Item item_of(const std::vector<DevGate> &run, size_t i) {
@@ -58,12 +58,16 @@ Item item_of(const std::vector<DevGate> &run, size_t i) {
   if (g.cls == GC_DENSE4) it.bits |= 1u << (int)g.tmask;
   it.bits |= (uint32_t)g.cmask;
   if (g.gmask != 0 || g.target < 0) it.blockable = false;
+  // The per-gate pass touches only the amplitudes whose local control bits are all 1 (and, for a phase, whose
+  // target bit is 1): the cost of the class, scaled by that fraction.
   switch (g.cls) {
     case GC_GENERAL: it.cost = 1.0; break;
     case GC_DENSE4: it.cost = 4.0; break;
     case GC_X: it.cost = 0.25; break;
-    default: it.cost = 0.5; break;  // diagonal, phase, anti-diagonal
+    case GC_PHASE: it.cost = 0.25; break;
+    default: it.cost = 0.5; break;  // diagonal, anti-diagonal
   }
+  it.cost = std::ldexp(it.cost, -__builtin_popcount((uint32_t)g.cmask));
   return it;
 }
 
@@ -166,6 +170,8 @@ void encode_planes(int mode, const double (*W)[kBlockK], unsigned char *dst) {
 
 } // namespace
 
+constexpr double kBlockPassShare = 0.75;
+
 size_t block_data_bytes(int mode) {
   return (size_t)(mode == MODE_C64_F32 ? kBlockSplitsC64 : kBlockDigitsC128) * kBlockPlaneBytes;
 }
@@ -179,6 +185,9 @@ int group_blocks(std::vector<DevGate> &run, int k, int mode, double min_cost, st
   for (size_t i = 0; i < run.size(); i += (run[i].cls == GC_DENSE4 ? 4 : 1)) items.push_back(item_of(run, i));
   std::vector<char> done(items.size(), 0);
   std::vector<DevGate> out;
+  const size_t data0 = data.size();
+  double total = 0.0, absorbed = 0.0;
+  for (const Item &it : items) total += it.cost;
   int nblocks = 0;
   for (size_t i = 0; i < items.size(); ++i) {
     if (done[i]) continue;
@@ -207,6 +216,7 @@ int group_blocks(std::vector<DevGate> &run, int k, int mode, double min_cost, st
       done[i] = 1;
       continue;
     }
+    absorbed += cost;
     for (int b = 0; b < k && __builtin_popcount(bits) < kBlockBits; ++b) bits |= 1u << b;
     int pos[kBlockBits], np = 0, slot[32];
     for (int b = 0; b < 32; ++b) slot[b] = 0;
@@ -231,6 +241,12 @@ int group_blocks(std::vector<DevGate> &run, int k, int mode, double min_cost, st
     h.gmask = off;  // offset in the plan's block data; made relative to the header by plan_blob_fill
     out.push_back(h);
     ++nblocks;
+  }
+  // A pass with blocks runs in the tensor-core kernel, where the remaining gates go one by one more slowly
+  // than in the per-gate pass: blocks are kept only if they take at least kBlockPassShare of the pass's work.
+  if (nblocks > 0 && absorbed < kBlockPassShare * total) {
+    data.resize(data0);
+    return 0;
   }
   run.swap(out);
   return nblocks;
