@@ -112,6 +112,25 @@ def test_tensor_blocks_are_ignored_where_they_do_not_apply():
     assert st["blocks"] == 0
 
 
+def test_passes_where_blocks_take_little_of_the_work_keep_the_per_gate_path():
+    # A pass keeps its blocks only if they take at least 3/4 of its per-gate work.  A CNOT and four dense gates
+    # on chunk bits 0-3 form a block (the CNOT first, so that the dense gates are not folded into a product
+    # start); twenty gates controlled by a qubit outside the chunk cannot join one, so with them the pass stays
+    # per-gate, and without them it runs the block.
+    rng = np.random.Generator(np.random.PCG64(23))
+    lead = [C.cnot(0, 1)] + [C.gate_u(C.haar_u2(rng), q) for q in range(4)]
+    tail = [C.gate_u(C.haar_u2(rng), 4 + i % 8, (15,)) for i in range(20)]
+    for dtype in (B.SV_C128, B.SV_C64):
+        gates = C.pack(lead + tail)
+        got, st = run(16, gates, dtype, True, 12)
+        assert st["blocks"] == 0, st
+        assert_close(got, run_oracle(16, gates), dtype, "per-gate pass, blocks on")
+        gates = C.pack(lead)
+        got, st = run(16, gates, dtype, True, 12)
+        assert st["blocks"] == 1, st
+        assert_close(got, run_oracle(16, gates), dtype, "one block")
+
+
 # ---- complex128: exact digit products ------------------------------------------------------------------
 
 @pytest.mark.parametrize("n,chunk_k", [(11, 11), (12, 11), (12, 12), (13, 12), (15, 11), (17, 12), (20, 12)])
