@@ -476,7 +476,8 @@ def run_ours(args):
         batched = {}
         for dt_b, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
             ks, picked = batch_chunk_sizes(B, [w.n for w in ws_b], dt_b, not args.no_autotune)
-            batched[name] = {**batched_measure(B, ws_b, dt_b, ks), "chunk_qubits": picked or "default"}
+            batched[name] = {**batched_measure(B, ws_b, dt_b, ks, tensor_blocks.get(B.SV_C128, 0)),
+                             "chunk_qubits": picked or "default"}
         batched["workload"] = "512 random circuits, n log-uniform in [10, 22], 10-40 layers, seed 1004"
         qft = {"qft20": qft_measure(B, "qft20", 5, 3, tensor_blocks.get(B.SV_C128, 0))}
         if args.n == N_QUBITS and not args.no_n33:
@@ -776,11 +777,13 @@ def batch_chunk_sizes(B, ns, dt, tune):
     return ks, picked
 
 
-def batched_measure(B, ws, dt, ks):
+def batched_measure(B, ws, dt, ks, tensor_blocks=0):
     """One sv_run_batch_k call over all circuits, end to end on the host clock (plan, allocate, upload, the
-    captured rounds, synchronise), after a warm-up call on the first 64 circuits."""
+    captured rounds, synchronise), after a warm-up call on the first 64 circuits; complex128 batches with
+    SV_OPT_TENSOR_BLOCKS = `tensor_blocks` (sv_batch_set_option)."""
     import torch
     ns, gl = [w.n for w in ws], [w.gates for w in ws]
+    B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, tensor_blocks if dt == B.SV_C128 else 0)
     for h in B.sv_run_batch(ns[:64], dt, gl[:64], chunk_k=ks[:64]):  # warm-up: kernels, allocator
         B.sv_destroy(h)
     torch.cuda.synchronize()
@@ -794,14 +797,17 @@ def batched_measure(B, ws, dt, ks):
     for h in hs:
         B.sv_destroy(h)
     gates_total = sum(len(g) for g in gl)
+    B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 0)
     return {"circuits": len(ws), "seconds": dt_s, "circuits_per_s": len(ws) / dt_s, "gates_per_s": gates_total / dt_s,
-            "rounds": st["rounds"], "mixed_rounds": st["mixed_rounds"], "max_round_chunks": st["max_round_chunks"],
-            "max_norm_deviation": dev}
+            "rounds": st["rounds"], "mixed_rounds": st["mixed_rounds"], "tensor_core_rounds": st["tc_rounds"],
+            "tensor_blocks_option": tensor_blocks if dt == B.SV_C128 else 0,
+            "max_round_chunks": st["max_round_chunks"], "max_norm_deviation": dev}
 
 
 def run_batched(args):
     """4096 independent random circuits (n log-uniform in [10, 22], 10-40 layers, seed 1004) in one
-    sv_run_batch_k call per dtype, chunk sizes from the autotuner per size class of n."""
+    sv_run_batch_k call per dtype, chunk sizes from the autotuner per size class of n; complex128 with
+    tensor-core blocks of >= 3 dense updates (--tensor-blocks overrides; 0 turns them off)."""
     from paper_1801_01037_gb300 import build as sv_build
     sv_build.build()
     from paper_1801_01037_gb300 import _binding as B
@@ -809,9 +815,10 @@ def run_batched(args):
     ws = C.batched_workloads(args.batch_count, seed=1004)
     ns = [w.n for w in ws]
     res = {}
+    tb = int(str(args.tensor_blocks).split(",")[0]) if args.tensor_blocks is not None else 3
     for dt, name in ((B.SV_C64, "c64"), (B.SV_C128, "c128")):
         ks, picked = batch_chunk_sizes(B, ns, dt, not args.no_autotune)
-        res[name] = {**batched_measure(B, ws, dt, ks), "chunk_qubits": picked or "default"}
+        res[name] = {**batched_measure(B, ws, dt, ks, tb), "chunk_qubits": picked or "default"}
     print(json.dumps({"metric": "batched random circuits: circuits/s (one sv_run_batch call, end to end)",
                       "workload": f"{len(ws)} circuits, n log-uniform in [10, 22], depth 10-40 layers, seed 1004",
                       "gates": sum(len(w.gates) for w in ws), "amplitudes": sum(2 ** n for n in ns), **res}),

@@ -300,13 +300,23 @@ sv_status sv_run_batch(int count, const int *n, sv_dtype dtype, const sv_gate *c
 sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, const sv_gate *const *gates,
                          const size_t *ngates, const int *chunk_k, void *stream, sv_state **out);
 
-/* Statistics of the last sv_run_batch / sv_run_batch_k call of this thread: rounds (launches of the batched
- * pass), rounds that ran in the FP64 / double-float split kernel (complex128 rounds with enough chunks to
- * fill the GPU several times), the largest and the total chunk count of a round. */
+/* Statistics of the last sv_run_batch / sv_run_batch_k call of this thread: rounds (steps of the batch: each
+ * advances every circuit by one pass), rounds that ran in the FP64 / double-float split kernel (complex128
+ * rounds with enough chunks to fill the GPU several times), the largest and the total chunk count of a round,
+ * and rounds with a tensor-core launch (passes with dense blocks, see sv_batch_set_option). */
 typedef struct sv_batch_stats {
-    uint64_t rounds, mixed_rounds, max_round_chunks, total_chunks;
+    uint64_t rounds, mixed_rounds, max_round_chunks, total_chunks, tc_rounds;
 } sv_batch_stats;
 sv_status sv_last_batch_stats(sv_batch_stats *out);
+
+/* Options for this host thread's later sv_run_batch / sv_run_batch_k calls (Sec. II.B's multi-qubit gates as
+ * matrices, applied as dense blocks).  Only SV_OPT_TENSOR_BLOCKS is accepted, with the values of
+ * sv_set_option (0, the default: off; 1: on; v >= 2: blocks must replace at least v dense one-qubit updates);
+ * it applies to complex128 batches in double-float arithmetic, to the circuits whose passes use chunks of 2^12
+ * amplitudes: their passes with blocks run in a tensor-core batched kernel beside the per-gate one in every
+ * round.  A wait for the tensor cores that runs out fails the batch with SV_ERR_TIMEOUT.  Errors: SV_ERR_ARG
+ * for another option or a value outside 0..64. */
+sv_status sv_batch_set_option(int option, int value);
 
 /* A serving loop on its own host thread and stream: admits requests while their states fit in
  * hbm_budget_bytes and fewer than max_active run, and advances every admitted request by one pass per

@@ -54,10 +54,10 @@ EXPORTED = [
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_run_batch_k", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version", "sv_last_batch_stats", "sv_server_pause",
-    "sv_server_get_stats", "sv_last_plan_blocks",
+    "sv_server_get_stats", "sv_last_plan_blocks", "sv_batch_set_option",
 ]
 
-BATCH_STATS_FIELDS = ["rounds", "mixed_rounds", "max_round_chunks", "total_chunks"]
+BATCH_STATS_FIELDS = ["rounds", "mixed_rounds", "max_round_chunks", "total_chunks", "tc_rounds"]
 SERVER_STATS_FIELDS = ["submitted", "admitted", "completed", "failed", "rounds", "mixed_rounds", "max_round_chunks",
                        "active", "pending", "budget_used"]
 
@@ -121,6 +121,7 @@ def load(path: str | None = None):
         "sv_server_pause": [P, i],
         "sv_server_get_stats": [P, P],
         "sv_last_plan_blocks": [P, P, P],
+        "sv_batch_set_option": [i, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -384,6 +385,11 @@ def sv_last_batch_stats() -> dict:
     v = (ctypes.c_uint64 * len(BATCH_STATS_FIELDS))()
     _check(load().sv_last_batch_stats(ctypes.cast(v, ctypes.c_void_p)))
     return dict(zip(BATCH_STATS_FIELDS, list(v)))
+
+
+def sv_batch_set_option(option: int, value: int) -> None:
+    """Set an option (SV_OPT_TENSOR_BLOCKS) for this thread's later sv_run_batch calls."""
+    _check(load().sv_batch_set_option(option, value))
 
 
 def sv_server_pause(srv: int, paused: bool) -> None:

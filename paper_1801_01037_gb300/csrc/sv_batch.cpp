@@ -32,18 +32,25 @@ int validate_circuit(int n, const sv_gate *g, size_t ng, std::string &why) {
   return SV_OK;
 }
 
-// Plan a circuit whose first pass synthesises |0...0>; every step is a fused pass.
-void plan_fresh(sv_state *s, const sv_gate *g, size_t ng, Plan &P) {
+// Plan a circuit whose first pass synthesises |0...0>; every step is a fused pass.  Dense tensor-core blocks
+// (tensor_blocks as SV_OPT_TENSOR_BLOCKS) only for complex128 double-float circuits with chunks of 2^kBatchTcK
+// amplitudes, the one chunk size the batched tensor-core kernel takes; other passes apply gates one by one.
+void plan_fresh(sv_state *s, const sv_gate *g, size_t ng, Plan &P, int tensor_blocks = 0) {
   PlanConfig cfg = plan_config(s);
   cfg.init_first = true;
   cfg.init_x = 0;
   cfg.single_as_sweep = false;
   cfg.fusion = true;
-  cfg.block_mode = -1;  // the batched kernels apply gates one by one
+  cfg.block_mode = -1;
+  if (tensor_blocks > 0 && mode_of(s) == MODE_C128_DF32 && cfg.k == kBatchTcK && s->n >= kBatchTcK) {
+    cfg.block_mode = MODE_C128_DF32;
+    if (tensor_blocks >= 2) cfg.block_min_cost = (double)tensor_blocks;
+  }
   make_plan(s->n, cfg, s->perm, g, ng, P);
 }
 
 thread_local sv_batch_stats t_batch_stats{};
+thread_local int t_batch_tensor_blocks = 0;
 
 // Grow-only device buffer.
 struct DevBuf {
@@ -60,6 +67,13 @@ struct DevBuf {
 };
 
 } // namespace
+
+extern "C" sv_status sv_batch_set_option(int option, int value) {
+  if (option != SV_OPT_TENSOR_BLOCKS) return set_error(SV_ERR_ARG, "only SV_OPT_TENSOR_BLOCKS applies to batches");
+  if (value < 0 || value > 64) return set_error(SV_ERR_ARG, "SV_OPT_TENSOR_BLOCKS must be in 0..64");
+  t_batch_tensor_blocks = value;
+  return SV_OK;
+}
 
 extern "C" sv_status sv_last_batch_stats(sv_batch_stats *out) {
   if (!out) return set_error(SV_ERR_ARG, "NULL argument");
@@ -129,11 +143,12 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
     states[i] = s;
   }
   // Plans are independent: several host threads make them.
+  const int tensor_blocks = t_batch_tensor_blocks;
   const int nthreads = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(16, (count + 31) / 32)));
   std::vector<std::thread> pool;
   for (int t = 0; t < nthreads; ++t)
     pool.emplace_back([&, t] {
-      for (int i = t; i < count; i += nthreads) plan_fresh(states[i], gates[i], ngates[i], plans[i]);
+      for (int i = t; i < count; i += nthreads) plan_fresh(states[i], gates[i], ngates[i], plans[i], tensor_blocks);
     });
   for (std::thread &th : pool) th.join();
   size_t max_rounds = 0;
@@ -147,24 +162,42 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
   }
   std::vector<unsigned char> blob(std::max<size_t>(blob_bytes, 16));
   for (int i = 0; i < count; ++i) plan_blob_fill(plans[i], blob.data() + blob_off[i]);
+  // Per round two launches: the passes that apply their gates one by one, and the passes with dense blocks
+  // (tensor-core kernel); each has its own descriptor list and chunk prefix sums.
   std::vector<PassDesc> descs;
+  std::vector<std::pair<int, int>> desc_src;  // (circuit, pass) of each descriptor
   std::vector<uint64_t> starts;
-  struct Round { size_t desc_off, start_off; int npass; uint64_t total; int kmax; };
+  struct Round {
+    size_t desc_off, start_off; int npass; uint64_t total; int kmax;
+    size_t tc_desc_off, tc_start_off; int tc_npass; uint64_t tc_total;
+  };
   std::vector<Round> rounds;
+  bool any_tc = false;
   for (size_t r = 0; r < max_rounds; ++r) {
-    Round R{descs.size(), starts.size(), 0, 0, 0};
-    for (int i = 0; i < count; ++i) {
-      if (r >= plans[i].passes.size()) continue;
-      PassDesc d = plans[i].passes[r];
-      d.psi = states[i]->psi;
-      d.init_x = (uint64_t)i;  // circuit index; replaced by the real fields below
-      descs.push_back(d);
-      starts.push_back(R.total);
-      R.total += 1ull << (d.n - d.k);
-      R.kmax = std::max(R.kmax, d.k);
-      ++R.npass;
+    Round R{descs.size(), starts.size(), 0, 0, 0, 0, 0, 0, 0};
+    for (int tc = 0; tc < 2; ++tc) {
+      if (tc) { starts.push_back(R.total); R.tc_desc_off = descs.size(); R.tc_start_off = starts.size(); }
+      for (int i = 0; i < count; ++i) {
+        // (plan_fresh forms blocks only in passes of 2^kBatchTcK-amplitude chunks)
+        if (r >= plans[i].passes.size() || (plans[i].passes[r].nblocks > 0) != (tc == 1)) continue;
+        PassDesc d = plans[i].passes[r];
+        d.psi = states[i]->psi;
+        descs.push_back(d);
+        desc_src.emplace_back(i, (int)r);
+        if (tc) {
+          starts.push_back(R.tc_total);
+          R.tc_total += 1ull << (d.n - d.k);
+          ++R.tc_npass;
+        } else {
+          starts.push_back(R.total);
+          R.total += 1ull << (d.n - d.k);
+          R.kmax = std::max(R.kmax, d.k);
+          ++R.npass;
+        }
+      }
     }
-    starts.push_back(R.total);
+    starts.push_back(R.tc_total);
+    any_tc |= R.tc_npass > 0;
     rounds.push_back(R);
   }
   DevBuf dg, dd, ds, dsched;
@@ -172,14 +205,13 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
       dd.ensure(std::max<size_t>(1, descs.size()) * sizeof(PassDesc), st) != SV_OK ||
       ds.ensure(std::max<size_t>(1, starts.size()) * sizeof(uint64_t), st) != SV_OK)
     return cleanup(set_error(SV_ERR_OOM, "batch descriptor allocation failed"));
-  for (size_t r = 0, di = 0; r < rounds.size(); ++r)
-    for (int i = 0; i < count; ++i) {
-      if (r >= plans[i].passes.size()) continue;
-      PassDesc &d = descs[di++];
-      plan_pass_pointers(plans[i], (int)r, (const unsigned char *)dg.p + blob_off[i], d);
-      d.init_x = plans[i].passes[r].init_x;
-    }
-  e = cudaMemcpyAsync(dg.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+  for (size_t di = 0; di < descs.size(); ++di) {
+    const int i = desc_src[di].first, r = desc_src[di].second;
+    plan_pass_pointers(plans[i], r, (const unsigned char *)dg.p + blob_off[i], descs[di]);
+  }
+  // the tensor-core kernel's error word (and the split kernel's counters, which it resets itself) start at 0
+  e = cudaMemsetAsync(dsched.p, 0, sizeof(FusedSched), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dg.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ds.p, starts.data(), starts.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   const int mode = default_mode(dtype);
@@ -194,12 +226,18 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
     for (size_t r = 0; r < rounds.size() && err == cudaSuccess; ++r) {
       const Round &R = rounds[r];
       int mixed = 0;
-      err = launch_fused_batch((const PassDesc *)dd.p + R.desc_off, (const uint64_t *)ds.p + R.start_off, R.npass,
-                               R.total, mode, R.kmax, q, kDefaultF64Share, (FusedSched *)dsched.p, &mixed);
+      if (R.npass > 0)
+        err = launch_fused_batch((const PassDesc *)dd.p + R.desc_off, (const uint64_t *)ds.p + R.start_off, R.npass,
+                                 R.total, mode, R.kmax, q, kDefaultF64Share, (FusedSched *)dsched.p, &mixed);
+      if (err == cudaSuccess && R.tc_npass > 0) {
+        err = launch_fused_batch_tc((const PassDesc *)dd.p + R.tc_desc_off, (const uint64_t *)ds.p + R.tc_start_off,
+                                    R.tc_npass, R.tc_total, q, (FusedSched *)dsched.p);
+        ++bs.tc_rounds;
+      }
       ++bs.rounds;
       bs.mixed_rounds += (uint64_t)mixed;
-      bs.max_round_chunks = std::max<uint64_t>(bs.max_round_chunks, R.total);
-      bs.total_chunks += R.total;
+      bs.max_round_chunks = std::max<uint64_t>(bs.max_round_chunks, R.total + R.tc_total);
+      bs.total_chunks += R.total + R.tc_total;
     }
     return err;
   };
@@ -207,7 +245,8 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
   if (e == cudaSuccess && rounds.size() > 1) {
     // Shared-memory grants are raised outside the capture.
     for (const Round &R : rounds)
-      if ((e = prepare_fused_batch(mode, R.kmax)) != cudaSuccess) break;
+      if (R.npass > 0 && (e = prepare_fused_batch(mode, R.kmax)) != cudaSuccess) break;
+    if (e == cudaSuccess && any_tc) e = prepare_fused_batch_tc();
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -236,6 +275,12 @@ extern "C" sv_status sv_run_batch_k(int count, const int *n, sv_dtype dtype, con
   }
   t_batch_stats = bs;
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "batched passes"));
+  if (any_tc) {
+    unsigned tc_err = 0;
+    e = cudaMemcpy(&tc_err, &((FusedSched *)dsched.p)->tc_err, sizeof tc_err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core error word"));
+    if (tc_err) return cleanup(set_error(SV_ERR_TIMEOUT, "a wait for the tensor cores ran out in a batched pass"));
+  }
   for (int i = 0; i < count; ++i) {
     states[i]->st_passes = (int)plans[i].passes.size();
     states[i]->st_fused = plans[i].n_fused_gates;

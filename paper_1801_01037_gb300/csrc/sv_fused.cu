@@ -973,19 +973,14 @@ __global__ void __launch_bounds__(kFusedThreads, min_blocks<MODE>()) k_fused(con
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) fused_chunk<MODE>(p, ch, sm, rowoff);
 }
 
-// Fused pass whose gates include dense blocks (GC_BLOCK) for the tensor cores.  Warp 0 allocates `ncols` TMEM
-// columns for the CTA's accumulators (ncols * CTAs per SM <= 512, so the allocation never waits on a CTA of
-// this launch), thread 0 initialises the mbarrier the MMAs commit to; both are released at the end.
+// Set-up of a tensor-core pass CTA for chunks of 2^k amplitudes: warp 0 allocates `ncols` TMEM columns for the
+// CTA's accumulators (ncols * CTAs per SM <= 512, so the allocation never waits on a CTA of this launch), the
+// first threads initialise the tiles' mbarriers the MMAs commit to, the zero plane in front of each pair's
+// complex128 digit planes is cleared; both the columns and the barriers are released by tc_teardown.
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, uint64_t nchunks, uint32_t ncols,
-                                                               unsigned *err) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  using S = typename Arith<MODE>::S;
-  S *sm = (S *)smraw;
-  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(S) << p.k));
-  const uint32_t R = 1u << (p.k - kBlockBits);
-  TcCtx tc;
-  tc.opA = smraw + tc_smem_base<MODE>(p.k);
+__device__ __forceinline__ void tc_setup(unsigned char *smraw, int k, uint32_t ncols, unsigned *err, TcCtx &tc) {
+  const uint32_t R = 1u << (k - kBlockBits);
+  tc.opA = smraw + tc_smem_base<MODE>(k);
   tc.opB = tc.opA + (size_t)tc_planes<MODE>() * R * kTcRowBytes;
   tc.mbar = reinterpret_cast<uint64_t *>(tc.opB + (size_t)kTcPairs * tc_bplanes<MODE>() * kBlockPlaneBytes);
   if constexpr (MODE != MODE_C64_F32) {
@@ -1014,6 +1009,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, ui
   tc.ok = 1;
   tc.err = err;
   tc.fixed_in = 0;
+}
+
+__device__ __forceinline__ void tc_teardown(const TcCtx &tc, uint32_t ncols) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(ncols) : "memory");
+}
+
+// Fused pass whose gates include dense blocks (GC_BLOCK) for the tensor cores.
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, uint64_t nchunks, uint32_t ncols,
+                                                               unsigned *err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  using S = typename Arith<MODE>::S;
+  S *sm = (S *)smraw;
+  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(S) << p.k));
+  TcCtx tc;
+  tc_setup<MODE>(smraw, p.k, ncols, err, tc);
   // The pass's gate records, copied once to shared memory (every chunk reads each of them); a pass with more
   // than kTcGateCopy records reads them from global memory.
   DevGate *gcopy = nullptr;
@@ -1026,10 +1040,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fused_tc(const PassDesc p, ui
   }
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
     fused_chunk<MODE, true, true, kTcThreads>(p, ch, sm, rowoff, &tc, gcopy);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(ncols) : "memory");
+  tc_teardown(tc, ncols);
 }
 
 // Complex128 pass split between the SM's two arithmetic units.  The double-float path keeps the FP32 pipes
@@ -1118,6 +1129,29 @@ __device__ __forceinline__ int batch_pass_of(const uint64_t *chunk_start, int np
     if (chunk_start[mid] <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Batched complex128 passes with dense blocks (double-float working form): every pass of the launch has chunks
+// of 2^kBatchTcK amplitudes; the round's chunks are numbered in order of their passes and chunk b belongs to
+// the last pass whose first chunk is <= b.  One CTA per SM, as k_fused_tc; the gate records are read from
+// global memory (the passes change from chunk to chunk).
+static_assert(kBatchTcK == kBlockBits + 8, "the batched tensor-core kernel is laid out for two 128-row tiles");
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_fused_batch_tc(const PassDesc *__restrict__ passes, const uint64_t *__restrict__ chunk_start, int npass,
+                     uint64_t total, uint32_t ncols, unsigned *err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ PassDesc sp;
+  float4 *sm = (float4 *)smraw;
+  uint64_t *rowoff = (uint64_t *)(smraw + ((size_t)sizeof(float4) << kBatchTcK));
+  TcCtx tc;
+  tc_setup<MODE_C128_DF32>(smraw, kBatchTcK, ncols, err, tc);
+  for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int lo = batch_pass_of(chunk_start, npass, b);
+    load_pass(sp, passes + lo);
+    fused_chunk<MODE_C128_DF32, true, true, kTcThreads>(sp, b - chunk_start[lo], sm, rowoff, &tc);
+  }
+  tc_teardown(tc, ncols);
 }
 
 __global__ void __launch_bounds__(kFusedThreads, SV_FUSED_MIN_BLOCKS)
@@ -1296,6 +1330,31 @@ cudaError_t prepare_fused_batch(int mode, int kmax) {
       if (e != cudaSuccess) return e;
       return ensure_smem((const void *)k_fused_batch_mixed, smem_bytes<MODE_C128_DF32>(kmax), batch_mixed_granted());
   }
+}
+
+// The batched tensor-core kernel's shared memory: the pass of 2^kBatchTcK amplitudes and its block planes.
+static std::atomic<int> *batch_tc_granted() {
+  static std::atomic<int> g[64] = {};
+  return g;
+}
+
+cudaError_t prepare_fused_batch_tc() {
+  return ensure_smem((const void *)k_fused_batch_tc, tc_smem_bytes<MODE_C128_DF32>(kBatchTcK), batch_tc_granted());
+}
+
+cudaError_t launch_fused_batch_tc(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,
+                                  cudaStream_t st, FusedSched *sched) {
+  if (total == 0 || npass == 0) return cudaSuccess;
+  if (sched == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = prepare_fused_batch_tc();
+  if (e != cudaSuccess) return e;
+  // two 128-row tiles of seven digit levels of 32 columns: 448 columns, allocated as 512
+  const uint32_t ncols = 512;
+  const uint64_t cap = (uint64_t)sms();
+  const unsigned grid = (unsigned)(total < cap ? total : cap);
+  k_fused_batch_tc<<<grid, kTcThreads, tc_smem_bytes<MODE_C128_DF32>(kBatchTcK), st>>>(d_passes, d_chunk_start, npass,
+                                                                                         total, ncols, &sched->tc_err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass, uint64_t total,

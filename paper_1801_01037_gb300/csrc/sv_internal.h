@@ -162,4 +162,12 @@ cudaError_t launch_fused_batch(const PassDesc *d_passes, const uint64_t *d_chunk
                                uint64_t total_chunks, int mode, int kmax, cudaStream_t st, int f64_share = 0,
                                FusedSched *sched = nullptr, int *used_mixed = nullptr);
 
+// Batched complex128 double-float passes with dense tensor-core blocks (every pass with k = kBatchTcK and blocks),
+// indexed as for launch_fused_batch.  A wait for the tensor cores that runs out sets sched->tc_err (never
+// cleared here).  prepare_fused_batch_tc raises the kernel's shared-memory grant outside a stream capture.
+constexpr int kBatchTcK = 12;
+cudaError_t prepare_fused_batch_tc();
+cudaError_t launch_fused_batch_tc(const PassDesc *d_passes, const uint64_t *d_chunk_start, int npass,
+                                  uint64_t total_chunks, cudaStream_t st, FusedSched *sched);
+
 } // namespace svi

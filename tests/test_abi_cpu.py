@@ -70,6 +70,16 @@ def test_null_and_range_errors_without_device(lib):
     assert b"NULL" in lib.sv_last_error()
 
 
+def test_batch_option_checks_without_device(lib):
+    from paper_1801_01037_gb300 import _binding as B
+    with pytest.raises(B.SvError):
+        B.sv_batch_set_option(B.SV_OPT_CHUNK_QUBITS, 12)
+    with pytest.raises(B.SvError):
+        B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 65)
+    B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 3)
+    B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 0)
+
+
 def test_no_device_is_reported_not_hidden(lib):
     import torch
     if torch.cuda.is_available():

@@ -33,6 +33,33 @@ def test_batch_matches_oracle_and_single_runs(dtype):
             B.sv_destroy(h)
 
 
+def test_c128_batch_with_tensor_core_blocks():
+    # Circuits from 10 to 18 qubits: those with chunks of 2^12 amplitudes (n >= 12) get dense blocks, run in
+    # the batched tensor-core kernel beside the per-gate kernel in the same rounds; the smaller ones and the
+    # ones given 2^10-amplitude chunks stay per-gate.  Every result against the oracle and against the same
+    # batch without blocks.
+    ws = C.batched_workloads(20, n_lo=10, n_hi=18, d_lo=4, d_hi=8, seed=91)
+    ns, gl = [w.n for w in ws], [w.gates for w in ws]
+    ks = [10 if i % 5 == 0 else 0 for i in range(len(ws))]
+    B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 3)
+    try:
+        hs = B.sv_run_batch(ns, B.SV_C128, gl, chunk_k=ks)
+        st = B.sv_last_batch_stats()
+    finally:
+        B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 0)
+    assert st["tc_rounds"] > 0 and st["tc_rounds"] <= st["rounds"], st
+    plain = B.sv_run_batch(ns, B.SV_C128, gl, chunk_k=ks)
+    assert B.sv_last_batch_stats()["tc_rounds"] == 0
+    try:
+        for w, h, h0 in zip(ws, hs, plain):
+            got = B.sv_read_amplitudes(h).astype(np.complex128)
+            assert_close(got, run_oracle(w.n, w.gates), B.SV_C128, w.name + " tensor-core batch")
+            assert_close(got, B.sv_read_amplitudes(h0).astype(np.complex128), B.SV_C128, w.name + " vs per-gate")
+    finally:
+        for h in hs + plain:
+            B.sv_destroy(h)
+
+
 def test_batch_with_empty_and_swap_only_circuits():
     gl = [C.pack([]), C.pack([C.gate_swap(0, 2)]), C.pack(C.ghz(5))]
     ns = [3, 3, 5]
