@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <cstdlib>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include "sv_internal.h"
@@ -375,6 +376,7 @@ struct TcCtx {
   float *red;           // kTcThreads / 32 floats of shared scratch (complex128 chunk norm)
   float sc, isc;        // complex128: 2^(47 - E) and 2^(E - 62) for the current chunk's exponent E
   int fixed_in;         // complex128: the chunk holds the previous block's output in fixed point (see below)
+  int no_mma;           // test hook: issue no MMA (every wait for the tensor cores then runs out)
 };
 
 // Row r's base slot (its index with zeros at the block bits, through the slot map).
@@ -724,7 +726,7 @@ __device__ __forceinline__ void tc_block(const DevGate &hdr, const DevGate *ghdr
       if (t == pair) cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       pair_sync(pair);
-      if ((tid & 255u) == 0 && ok) tc_issue<MODE>(tc, t, R, myB);
+      if ((tid & 255u) == 0 && ok && !tc.no_mma) tc_issue<MODE>(tc, t, R, myB);
     }
     for (uint32_t t = pair; t < ntiles; t += kTcPairs) {
       if (ok) ok = tc_wait(tc.mbar + t, tc.phase) ? 1 : 0;
@@ -859,6 +861,7 @@ __device__ __forceinline__ void fused_chunk(const PassDesc &p, uint64_t chunk, t
     tc_chunk_scale(sm, nloc, *tc);
     tc->fixed_in = 0;
   }
+  if constexpr (TC) tc->no_mma = p.tc_flags & 1;
 
   // Tensor-core passes apply an exchange (X) with no control inside the chunk lazily: the pending exchanges
   // form a mask xm, amplitude j of the chunk sits in slot slot(j ^ xm) (slot is linear over GF(2)), blocks read
@@ -1009,6 +1012,7 @@ __device__ __forceinline__ void tc_setup(unsigned char *smraw, int k, uint32_t n
   tc.ok = 1;
   tc.err = err;
   tc.fixed_in = 0;
+  tc.no_mma = 0;
 }
 
 __device__ __forceinline__ void tc_teardown(const TcCtx &tc, uint32_t ncols) {
@@ -1277,7 +1281,11 @@ cudaError_t tc_launch(const PassDesc &p, cudaStream_t st, FusedSched *sched) {
   const uint64_t nchunks = 1ull << (p.n - p.k);
   const uint64_t cap = (uint64_t)sms() * occ;
   const unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
-  k_fused_tc<MODE><<<grid, kTcThreads, smem, st>>>(p, nchunks, ncols, &sched->tc_err);
+  // Test hook: with SV_TEST_TC_NO_MMA set no MMA is issued, so the kernel's bounded waits run out and the
+  // state reports SV_ERR_TIMEOUT (the failure path of a tensor core that never answers, without a fault).
+  PassDesc q = p;
+  q.tc_flags = std::getenv("SV_TEST_TC_NO_MMA") ? 1 : 0;
+  k_fused_tc<MODE><<<grid, kTcThreads, smem, st>>>(q, nchunks, ncols, &sched->tc_err);
   return cudaGetLastError();
 }
 

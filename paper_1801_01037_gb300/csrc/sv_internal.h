@@ -92,7 +92,7 @@ struct PassDesc {
   int32_t permuted;       // 1 if qpos_out differs from qpos
   int8_t src_bit[16];     // permuted: bit j of the local amplitude stored at slot o is bit src_bit[j] of o
   int32_t nblocks;        // GC_BLOCK records among the gates (> 0: the pass needs the tensor-core kernel)
-  int32_t reserved;
+  int32_t tc_flags;      // tensor-core passes, test hook only: 1 = issue no MMA, so every wait runs out
 };
 static_assert(sizeof(PassDesc) == 112, "PassDesc layout");
 

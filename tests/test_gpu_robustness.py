@@ -64,3 +64,32 @@ def test_write_amplitudes_rejects_values_outside_the_arithmetic(dtype):
             assert B.sv_read_amplitudes(h)[3] == 2.0 ** 125
     finally:
         B.sv_destroy(h)
+
+
+def test_tensor_core_wait_that_runs_out_is_reported(monkeypatch):
+    # With SV_TEST_TC_NO_MMA set, the tensor-core pass issues no MMA, so the mbarrier it waits on never
+    # completes: every wait is bounded (2 s), the kernel records the time-out, skips its remaining blocks and
+    # returns, and the state's next read reports SV_ERR_TIMEOUT.  The context stays usable: the same circuit
+    # on a new state afterwards matches the oracle.
+    n = 13
+    w = C.random_workload(n, 4, seed=31)
+    monkeypatch.setenv("SV_TEST_TC_NO_MMA", "1")
+    h = B.sv_create(n, B.SV_C128)
+    try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1)
+        B.sv_apply_circuit(h, w.gates)
+        assert B.sv_last_plan_blocks(h)["blocks"] > 0
+        with pytest.raises(B.SvError) as ei:
+            B.sv_read_amplitudes(h)
+        assert ei.value.code == B.SV_ERR_TIMEOUT
+    finally:
+        B.sv_destroy(h)
+    monkeypatch.delenv("SV_TEST_TC_NO_MMA")
+    h = B.sv_create(n, B.SV_C128)
+    try:
+        B.sv_set_option(h, B.SV_OPT_TENSOR_BLOCKS, 1)
+        B.sv_apply_circuit(h, w.gates)
+        got = B.sv_read_amplitudes(h)
+    finally:
+        B.sv_destroy(h)
+    assert_close(got, run_oracle(n, w.gates), B.SV_C128, "after a time-out")
