@@ -102,12 +102,15 @@ typedef struct sv_server sv_server;
 #define SV_OPT_TENSOR_BLOCKS 10 /* 1 = compose runs of gates on at most 4 chunk bits into one 16 x 16 unitary
                                    (FP64, host; Sec. II.B's multi-qubit gate as a matrix) and apply it with
                                    tcgen05 tensor-core MMAs; 0 = per-gate arithmetic (the default).
-                                   complex64: three bfloat16 splits of each factor (24 bits), FP32 accumulation.
+                                   complex64: three bfloat16 splits of each factor (24 bits), FP32 accumulation
+                                   on the tensor cores, which drifts the state's norm by about 3e-7 per block
+                                   (per-gate passes: far less), so the library's autotuner leaves it off.
                                    complex128 (double-float arithmetic, chunks of at most 2^12): six exact
                                    base-256 digits of each factor, integer products accumulated exactly per
                                    digit level in FP32 and combined in double-float (error a few 2^-47 of the
                                    chunk's 2-norm per block).  Used for fused passes with chunks of at least
-                                   2^11 amplitudes.  A value v >= 2 turns blocks on and keeps only blocks that
+                                   2^11 amplitudes, in passes where the blocks take at least 3/4 of the
+                                   per-gate work.  A value v >= 2 turns blocks on and keeps only blocks that
                                    replace at least v dense one-qubit gate updates (1: at least 2). */
 
 /* ---------------------------------------------------------------------------------------------------------
