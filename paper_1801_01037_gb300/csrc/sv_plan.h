@@ -65,8 +65,9 @@ int validate_gate(const sv_gate &g, int n, std::string &why);
 void group_cubes(const std::vector<DevGate> &run, int k, std::vector<DevGate> &out);
 
 // Replace runs of a pass's gates (chunk-local targets, in order) by dense blocks on kBlockBits bits where that
-// saves at least `min_cost` dense one-qubit updates; appends each block's operand planes to `data` (header
-// gmask = their offset there).  Returns the number of blocks.
+// saves at least `min_cost` dense one-qubit updates of the chunk; appends each block's operand planes to `data`
+// (header gmask = their offset there).  The pass keeps its blocks only if they take at least 3/4 of its
+// per-gate work (else `run` and `data` are left as they were).  Returns the number of blocks.
 int group_blocks(std::vector<DevGate> &run, int k, int mode, double min_cost, std::vector<unsigned char> &data);
 size_t block_data_bytes(int mode);
 
