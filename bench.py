@@ -422,8 +422,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         st = B.sv_last_plan_stats(h)
+        st_blk = B.sv_last_plan_blocks(h)
     finally:
         B.sv_destroy(h)
+    # bytes of the plan's device blob uploaded per step: one 192-byte record per fused gate (a block's header
+    # replaces its gates; the bench circuit has no two-qubit gates), then, 128-byte aligned, 6 digit planes of
+    # 2 KiB per complex128 block; sweeps take their record as a kernel parameter
+    records = st["fused_gates"] - st_blk["block_gates"] + st_blk["blocks"]
+    blob_bytes = ((records * 192 + 127) // 128 * 128 + st_blk["blocks"] * 6 * 2048) if st_blk["blocks"] else records * 192
 
     t_max = max_over_ranks(dist, c128["ms"]) / 1e3
     total_gates = sum_over_ranks(dist, G * args.steps)
@@ -578,11 +584,12 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "accuracy": accuracy,
         "e2e": {"value": e2e_value, "unit": "gates/s",
-                "h2d_bytes_per_step": (st["fused_gates"] + st["sweep_gates"]) * 192 + (96 * args.n if st["absorbed"] else 0),
+                "h2d_bytes_per_step": blob_bytes + st["sweep_gates"] * 192 + (96 * args.n if st["absorbed"] else 0),
                 "d2h_bytes_per_step": 8 + READ_COUNT * 16,
-                "note": "h2d: the planned 192-byte device gate records, uploaded per step (a single-gate sweep "
-                        "takes its record as a kernel parameter), plus 96 B per qubit of product-start factors; "
-                        "d2h: the FP64 norm and 1024 amplitudes"},
+                "note": "h2d: the plan's device blob uploaded per step (192-byte gate records, block headers and "
+                        "the blocks' 12 KiB of digit planes each; a single-gate sweep takes its record as a kernel "
+                        "parameter), plus 96 B per qubit of product-start factors; d2h: the FP64 norm and 1024 "
+                        "amplitudes"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": c128["clocks"],
         "norm_last_step": c128["norm"],
