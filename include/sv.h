@@ -278,6 +278,15 @@ sv_status sv_sync(sv_state *s);
 sv_status sv_last_plan_stats(sv_state *s, int *passes, int *fused_gates, int *sweep_gates, int *relabels,
                              int *remaps, int *absorbed);
 
+/* Host-only dry run of the dense-block planner (Sec. II.B: a run of gates on a few qubits as one matrix on
+ * them) for `ngates` records on n qubits of `dtype`, from the identity layout, as a state with chunk size
+ * chunk_k (0: the default) and SV_OPT_TENSOR_BLOCKS = tensor_blocks would plan them: fused passes, passes that
+ * hold blocks, blocks, and the source gates they replace.  No device work; works without a GPU.  Output
+ * pointers may be NULL.  Errors: SV_ERR_ARG (sizes, options), SV_ERR_NOT_UNITARY (as sv_apply_circuit). */
+sv_status sv_plan_dry_run_blocks(int n, sv_dtype dtype, int chunk_k, int tensor_blocks, const sv_gate *gates,
+                                 size_t ngates, int *passes, int *passes_with_blocks, int *blocks,
+                                 int *block_gates);
+
 /* Dense tensor-core blocks (SV_OPT_TENSOR_BLOCKS) of the last apply call: blocks applied and source gates they
  * replaced.  Any pointer may be NULL. */
 sv_status sv_last_plan_blocks(sv_state *s, int *blocks, int *block_gates);

@@ -54,7 +54,7 @@ EXPORTED = [
     "sv_apply_circuit_graph", "sv_read_amplitudes", "sv_read_amplitudes_at", "sv_read_probabilities", "sv_sample", "sv_expect_z", "sv_norm", "sv_norm_noalloc",
     "sv_renormalize", "sv_sync", "sv_last_plan_stats", "sv_plan_dry_run", "sv_profile_last", "sv_run_batch", "sv_run_batch_k", "sv_server_create", "sv_server_destroy",
     "sv_submit", "sv_poll", "sv_last_error", "sv_version", "sv_last_batch_stats", "sv_server_pause",
-    "sv_server_get_stats", "sv_last_plan_blocks", "sv_batch_set_option",
+    "sv_server_get_stats", "sv_last_plan_blocks", "sv_batch_set_option", "sv_plan_dry_run_blocks",
 ]
 
 BATCH_STATS_FIELDS = ["rounds", "mixed_rounds", "max_round_chunks", "total_chunks", "tc_rounds"]
@@ -122,6 +122,7 @@ def load(path: str | None = None):
         "sv_server_get_stats": [P, P],
         "sv_last_plan_blocks": [P, P, P],
         "sv_batch_set_option": [i, i],
+        "sv_plan_dry_run_blocks": [i, i, i, i, P, sz, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -385,6 +386,15 @@ def sv_last_batch_stats() -> dict:
     v = (ctypes.c_uint64 * len(BATCH_STATS_FIELDS))()
     _check(load().sv_last_batch_stats(ctypes.cast(v, ctypes.c_void_p)))
     return dict(zip(BATCH_STATS_FIELDS, list(v)))
+
+
+def sv_plan_dry_run_blocks(n: int, dtype: int, gates: np.ndarray, tensor_blocks: int, chunk_k: int = 0) -> dict:
+    """Host-only dry run of the dense-block planner: {passes, passes_with_blocks, blocks, block_gates}."""
+    g = _gate_array(gates)
+    out = [ctypes.c_int() for _ in range(4)]
+    _check(load().sv_plan_dry_run_blocks(n, dtype, chunk_k, tensor_blocks, g.ctypes.data if g.size else None, g.size,
+                                         *[ctypes.byref(v) for v in out]))
+    return dict(zip(("passes", "passes_with_blocks", "blocks", "block_gates"), (v.value for v in out)))
 
 
 def sv_batch_set_option(option: int, value: int) -> None:

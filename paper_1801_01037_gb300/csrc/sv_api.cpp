@@ -648,6 +648,38 @@ sv_status sv_plan_dry_run(int n, sv_dtype dtype, int chunk_k, const sv_gate *gat
   return SV_OK;
 }
 
+sv_status sv_plan_dry_run_blocks(int n, sv_dtype dtype, int chunk_k, int tensor_blocks, const sv_gate *gates,
+                                 size_t ngates, int *passes, int *passes_with_blocks, int *blocks, int *block_gates) {
+  if (n < 1 || n > kMaxQubits) return set_error(SV_ERR_ARG, "n must be in [1, 36]");
+  if (bad_dtype(dtype)) return set_error(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+  if (tensor_blocks < 0 || tensor_blocks > 64) return set_error(SV_ERR_ARG, "tensor_blocks must be in 0..64");
+  if (chunk_k != 0 && (chunk_k < 6 || chunk_k > kMaxChunkQubits))
+    return set_error(SV_ERR_ARG, "chunk_k must be 0 or 6..13");
+  if (!gates && ngates) return set_error(SV_ERR_ARG, "gates is NULL");
+  {
+    std::string why;
+    size_t bad = 0;
+    const int rc = validate_records(gates, ngates, n, why, bad);
+    if (rc != SV_OK) return set_error(rc, "gate " + std::to_string(bad) + ": " + why);
+  }
+  sv_state tmp;
+  tmp.n = n;
+  tmp.dtype = dtype;
+  tmp.chunk_k = chunk_k;
+  tmp.tensor_blocks = tensor_blocks;
+  std::vector<int> perm(n);
+  for (int t = 0; t < n; ++t) perm[t] = t;
+  Plan P;
+  make_plan(n, plan_config(&tmp), perm, gates, ngates, P);
+  int with = 0;
+  for (const PassDesc &d : P.passes) with += d.nblocks > 0;
+  if (passes) *passes = (int)P.passes.size();
+  if (passes_with_blocks) *passes_with_blocks = with;
+  if (blocks) *blocks = P.n_blocks;
+  if (block_gates) *block_gates = P.n_block_gates;
+  return SV_OK;
+}
+
 sv_status sv_last_plan_blocks(sv_state *s, int *blocks, int *block_gates) {
   if (!s) return set_error(SV_ERR_ARG, "state is NULL");
   if (blocks) *blocks = s->st_blocks;

@@ -80,6 +80,36 @@ def test_batch_option_checks_without_device(lib):
     B.sv_batch_set_option(B.SV_OPT_TENSOR_BLOCKS, 0)
 
 
+def test_block_planner_dry_run(lib):
+    """The dense-block planner through the C ABI, on the host: random layers form blocks on chunks of 2^11 and
+    2^12 amplitudes (and 2^13 for complex64), each block replacing at least two gates; nothing forms without the
+    option, with chunks below one 128-row tile, or for complex128 chunks of 2^13; the QFT's passes of controlled
+    phases stay per-gate (blocks would take less than 3/4 of a pass's work); a pass whose dense gates all sit on
+    four chunk bits forms exactly one block unless twenty gates with a control outside the chunk follow them."""
+    from paper_1801_01037_gb300 import _binding as B
+    w = C.random_workload(16, 6, seed=12)
+    for dtype, k in ((B.SV_C128, 11), (B.SV_C128, 12), (B.SV_C64, 12), (B.SV_C64, 13)):
+        r = B.sv_plan_dry_run_blocks(16, dtype, w.gates, 3, chunk_k=k)
+        assert r["blocks"] > 0 and r["block_gates"] >= 2 * r["blocks"], (dtype, k, r)
+        assert 0 < r["passes_with_blocks"] <= r["passes"]
+        assert B.sv_plan_dry_run_blocks(16, dtype, w.gates, 0, chunk_k=k)["blocks"] == 0
+    assert B.sv_plan_dry_run_blocks(16, B.SV_C128, w.gates, 3, chunk_k=13)["blocks"] == 0
+    assert B.sv_plan_dry_run_blocks(16, B.SV_C64, w.gates, 3, chunk_k=10)["blocks"] == 0
+    assert B.sv_plan_dry_run_blocks(10, B.SV_C64, C.random_workload(10, 4, seed=3).gates, 1)["blocks"] == 0
+    q = C.qft_workload(20, seed=1001)
+    assert B.sv_plan_dry_run_blocks(20, B.SV_C128, q.gates, 3)["blocks"] == 0
+    rng = np.random.Generator(np.random.PCG64(23))
+    lead = [C.cnot(0, 1)] + [C.gate_u(C.haar_u2(rng), t) for t in range(4)]
+    tail = [C.gate_u(C.haar_u2(rng), 4 + i % 8, (15,)) for i in range(20)]
+    r = B.sv_plan_dry_run_blocks(16, B.SV_C128, C.pack(lead), 1, chunk_k=12)
+    assert (r["blocks"], r["block_gates"]) == (1, 5), r
+    assert B.sv_plan_dry_run_blocks(16, B.SV_C128, C.pack(lead + tail), 1, chunk_k=12)["blocks"] == 0
+    # a block replaces gates only up to its minimum size: 5 gates worth 4.125 dense updates
+    assert B.sv_plan_dry_run_blocks(16, B.SV_C128, C.pack(lead), 5, chunk_k=12)["blocks"] == 0
+    with pytest.raises(B.SvError):
+        B.sv_plan_dry_run_blocks(16, B.SV_C128, w.gates, 65)
+
+
 def test_no_device_is_reported_not_hidden(lib):
     import torch
     if torch.cuda.is_available():
